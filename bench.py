@@ -1,0 +1,350 @@
+"""Benchmark: clause x assignment all-F tests on one GB300 (or N, one process each).
+
+Workload (default): plain test, single instance -- 1M variables, 4M clauses with
+lognormal sizes (median 20, sigma 1, clamped to [2, 500]) over Zipf(1.1) variables,
+1024 trail-prefix-correlated assignments in 32 groups (30-70 % assigned), 10k planted
+hits; seeded synthetic data.  One step = one GPU run of the method over a resident
+clause database: pack the step's assignment set (codes already in HBM) into planes,
+test every clause against every assignment, compact the hits into report records and
+read back their count.  value = clauses x assignments tested per second (G/s).
+
+e2e: the same step through the public API from pinned HOST memory: the codes go
+host->device inside the timed region and the records come back device->host.
+
+--impl reference runs the oracle (plain C on the host cores) on a bounded sample of
+the same workload, the reference arm of this comparison.
+
+Under torchrun each rank holds its own 4M-clause database (seed + rank) and tests the
+same assignment set: per-GPU work is fixed (weak scaling); ranks never exchange data
+except the timing barrier and the max-over-ranks reduction.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "clause×assignment tests/s (G/s) + HBM roofline fraction; served p50/p99 latency"
+UNIT = "G tests/s"
+WORKLOAD = ("plain test, single instance: 1M vars, 4M clauses, lognormal sizes (median 20, cap 500), "
+            "Zipf(1.1) vars; 1024 assignments as 32 trail-prefix groups, 30-70% assigned; 10k planted hits")
+
+
+def peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def kernel_source_sha(name: str) -> str:
+    src = open(os.path.join(ROOT, "paper_2012_03119_gb300", "csrc", name), "rb").read()
+    return hashlib.sha256(src).hexdigest()[:16]
+
+
+def profiled_traffic(kernel_file: str, summary: str) -> float | None:
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current source."""
+    p = os.path.join(ROOT, "profiles", summary)
+    if not os.path.exists(p):
+        return None
+    text = open(p).read()
+    m_sha = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
+    m_b = re.search(r"dram_bytes_per_launch_full:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_b or m_sha.group(1) != kernel_source_sha(kernel_file):
+        return None
+    return float(m_b.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the benchmark runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "100"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_instance(config: str, rank: int, scale: float):
+    import synth
+    if config == "single":
+        inst = synth.single(scale=scale, seed=synth.seed_for(2, rank))
+        if rank:  # every rank tests the same assignment set against its own clauses
+            inst.codes = synth.single(scale=scale, seed=synth.seed_for(2, 0)).codes
+        return inst, WORKLOAD if scale == 1.0 else f"{WORKLOAD} (scaled x{scale:g})"
+    if config == "structured":
+        return synth.structured(scale=scale, seed=synth.seed_for(5, rank)), (
+            "large structured: 10M vars in 1,000 communities, 10M clauses, lognormal sizes (median 40, cap 1000), "
+            f"1024 trail assignments (scaled x{scale:g})")
+    if config == "tiny":
+        return synth.tiny(), "plain test, tiny: 2,000 vars, 20,000 clauses, 64 assignments"
+    raise SystemExit(f"unknown config {config}")
+
+
+def algorithmic_bytes(inst, n_records: int) -> dict:
+    """Bytes the method must move per launch.
+    test: 4(m+1) + 4L + 2*V*W*4 + 12*R (offsets, every literal once, each plane row once, records);
+    pack: N*V + 2*V*W*4 (codes in, planes out)."""
+    m, L, V, N = inst.n_clauses, inst.n_lits, inst.n_vars, inst.n_assign
+    W = (N + 31) // 32
+    return {"test": 4 * (m + 1) + 4 * L + 2 * V * W * 4 + 12 * n_records, "pack": N * V + 2 * V * W * 4}
+
+
+def cpu_baseline(inst, max_seconds: float = 15.0) -> dict:
+    """The oracle, as it stands, on the host cores over a bounded sample of assignments."""
+    import oracle
+    threads = os.cpu_count() or 1
+    n = 32
+    t0 = time.perf_counter()
+    oracle.allf_pairs(inst.offsets, inst.lits, inst.codes, a_range=(0, n), threads=threads)
+    dt = time.perf_counter() - t0
+    n2 = int(min(inst.n_assign, max(n, n * max_seconds / max(dt, 1e-3) * 0.8)) // 32 * 32) or 32
+    if n2 > n:
+        t0 = time.perf_counter()
+        oracle.allf_pairs(inst.offsets, inst.lits, inst.codes, a_range=(0, n2), threads=threads)
+        dt = time.perf_counter() - t0
+        n = n2
+    return {"value": inst.n_clauses * n / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"all {inst.n_clauses} clauses x assignments [0, {n}) ({n / inst.n_assign:.3g} of the set), "
+                      f"{dt:.2f} s wall on {threads} threads"}
+
+
+def run_reference(args, inst, workload):
+    """Reference arm: the oracle on the host cores, one bounded sample per step."""
+    import oracle
+    threads = os.cpu_count() or 1
+    n = max(32, min(inst.n_assign, args.ref_assignments))
+    if args.warmup > 0:
+        oracle.allf_pairs(inst.offsets, inst.lits, inst.codes, a_range=(0, 32), threads=threads)
+    times = []
+    for k in range(args.steps):
+        lo = (k * n) % inst.n_assign
+        hi = min(inst.n_assign, lo + n)
+        t0 = time.perf_counter()
+        oracle.allf_pairs(inst.offsets, inst.lits, inst.codes, a_range=(lo, hi), threads=threads)
+        times.append((time.perf_counter() - t0, hi - lo))
+    tot_t = sum(t for t, _ in times)
+    tot_u = sum(inst.n_clauses * a for _, a in times)
+    value = tot_u / tot_t / 1e9
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": workload, "sample_per_step": f"all clauses x {n} assignments"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"all {inst.n_clauses} clauses x {n} assignments per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gss", choices=["gss", "reference"])
+    ap.add_argument("--config", default="single", choices=["single", "structured", "tiny"])
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--ref-assignments", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        inst, workload = make_instance(args.config, 0, args.scale)
+        print(json.dumps(run_reference(args, inst, workload)), flush=True)
+        return
+
+    import torch
+    import paper_2012_03119_gb300 as gss
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    warmup = max(3, args.warmup)
+    inst, workload = make_instance(args.config, rank, args.scale)
+    stream = torch.cuda.Stream()
+    N, V, m = inst.n_assign, inst.n_vars, inst.n_clauses
+    cap = max(1 << 22, 8 * len(inst.planted) + 4 * m)
+    ctx = gss.Context(V, device=local, stream=stream, report_capacity=cap, max_assignments=max(N, 32))
+
+    # a-1: ingest the database (once; the database stays resident like the paper's GPU clause store)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.add_clauses(inst.offsets, inst.lits)
+    ingest_s = time.perf_counter() - t0
+
+    d_codes = torch.from_numpy(inst.codes).to(f"cuda:{local}")
+    torch.cuda.synchronize()
+    pitch = V
+
+    def step():
+        gss.gss_set_assignments_device(ctx.ptr, d_codes.data_ptr(), pitch, N)
+        ctx.test()
+
+    # correctness guard outside timing: every planted pair is reported
+    step()
+    rec = ctx.fetch_reports()
+    pairs = gss.expand_reports(rec)
+    key = set((pairs[:, 0].astype(np.int64) << 32 | pairs[:, 1]).tolist())
+    planted_ok = all(((int(c) << 32) | int(a)) in key for c, a in inst.planted.tolist())
+    n_records = len(rec)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    for _ in range(warmup):
+        step()
+        ctx.report_count()
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start.record(stream)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        gss.gss_set_assignments_device(ctx.ptr, d_codes.data_ptr(), pitch, N)
+        ev[k][1].record(stream)
+        ctx.test()
+        ev[k][2].record(stream)
+        ctx.report_count()  # the step's result (record count) read back to the host
+    end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    elapsed = start.elapsed_time(end) / 1e3
+    t_pack = float(np.mean([e[0].elapsed_time(e[1]) for e in ev])) / 1e3
+    t_test = float(np.mean([e[1].elapsed_time(e[2]) for e in ev])) / 1e3
+    if dist:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+
+    # e2e through the public API from pinned host memory
+    e2e_steps = args.e2e_steps or max(3, min(args.steps, 20))
+    h_codes = torch.empty((N, V), dtype=torch.uint8).pin_memory()
+    h_codes.numpy()[:] = inst.codes
+    h_rec = torch.empty((cap * 12,), dtype=torch.uint8).pin_memory().numpy().view(gss.REPORT_DTYPE)
+    for _ in range(2):
+        ctx.set_assignments(h_codes.numpy())
+        ctx.test()
+        ctx.fetch_reports(h_rec)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.set_assignments(h_codes.numpy())
+        ctx.test()
+        ctx.fetch_reports(h_rec)
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    clk = clocks.stop()
+
+    units = m * N * world
+    value = units * args.steps / elapsed / 1e9
+    pk = peaks()
+    B = algorithmic_bytes(inst, n_records)
+    roof = {
+        "pack": {"bound": "hbm", "achieved": B["pack"] / t_pack / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                 "frac": B["pack"] / t_pack / 1e9 / pk["hbm_gbs"], "time_us": t_pack * 1e6, "bytes": B["pack"],
+                 "traffic": profiled_traffic("k_pack.cu", "k_pack__single_V1M_N1024.md"), "kernel": "k_pack",
+                 "peak_source": f"{pk['source']} hbm_gbs"},
+        "test": {"bound": "hbm", "achieved": B["test"] / t_test / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                 "frac": B["test"] / t_test / 1e9 / pk["hbm_gbs"], "time_us": t_test * 1e6, "bytes": B["test"],
+                 "traffic": profiled_traffic("k_test.cu", "k_test__single_V1M_N1024.md"), "kernel": "k_test",
+                 "peak_source": f"{pk['source']} hbm_gbs"},
+    }
+    dominant = "pack" if t_pack >= t_test else "test"
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": warmup,
+        "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": workload, "n_vars": V, "n_clauses": m, "n_lits": inst.n_lits, "n_assign": N,
+                   "seed": inst.params.get("seed"), "l2": "inputs larger than L2 (1 GB codes + 0.26 GB planes "
+                   "streamed per step)" if args.config == "single" and args.scale == 1.0 else "see sizes",
+                   "parallelism": f"weak x{world}: one clause database per GPU, shared assignment set"},
+        "e2e": {"value": units * e2e_steps / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": N * V,
+                "d2h_bytes_per_step": 12 * n_records + 48},
+        "roofline": {k: v for k, v in roof[dominant].items()},
+        "roofline_all": roof,
+        "kernel_only": {"test_tests_per_s_G": m * N / t_test / 1e9, "pack_us": t_pack * 1e6,
+                        "test_us": t_test * 1e6},
+        "ingest": {"seconds": ingest_s, "clauses": m, "lits": inst.n_lits,
+                   "GB_per_s": (8 * (m + 1) + 4 * inst.n_lits) / ingest_s / 1e9},
+        "gpu_launches": 2 * args.steps,
+        "records": n_records, "pairs": int(len(pairs)), "planted_found": planted_ok,
+        "clocks": clk,
+    }
+    ctx.close()
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(inst)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,205 @@
+/*
+ * gss.h -- C ABI of the GB300 clause x assignment test library (libgss.so).
+ *
+ * The library tests a resident database of clauses against a set of
+ * three-valued assignments at once and reports every (clause, assignment) pair
+ * in which every literal of the clause is F under the assignment -- the pairs
+ * where the clause "would have been in conflict" (Section 3.3), i.e. the
+ * allFalse output of Listing assignmentTrigger (Section 3.4), evaluated over
+ * many clauses in parallel and 32 assignments per machine word (Section 3.5).
+ * GSS_MODE_TRIGGER switches the test to Definition "triggers" (Section 3.3):
+ * no literal T and at least s - 1 of the s literals F.
+ *
+ * Notation.  V variables 0..V-1; literal l = 2v + s, s = 1 meaning "not v";
+ * value codes 0 = U, 1 = T, 2 = F (Section 3.1: truth values {T, F, U},
+ * not T = F, not F = T, not U = U, A(not v) = not A(v)).  N assignments per
+ * set; assignment a lives in 32-bit word a / 32, bit a % 32.
+ *
+ * Conventions.
+ *   - Every call returns an int status (GSS_OK or a negative GSS_E_* code);
+ *     no C++ exception crosses the ABI.  gss_last_error() gives the message.
+ *   - Host pointers stay owned by the caller and may be released as soon as
+ *     the call returns.  Device pointers passed in stay owned by the caller
+ *     and must stay valid until the work that reads them has completed on the
+ *     context's stream.  All device memory the library allocates is owned by
+ *     the context and released by gss_destroy().
+ *   - Device work is queued on the context's stream (gss_config.stream, or a
+ *     stream the context creates).  Calls that return results to the host
+ *     (gss_fetch_reports, gss_report_count) synchronise that stream.
+ *   - One context must not be used by two host threads at the same time.
+ *   - Clause ids are dense and assigned in insertion order starting at 0.
+ */
+#ifndef GSS_H
+#define GSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ codes */
+enum {
+  GSS_OK = 0,
+  GSS_E_INVAL = -1,     /* bad argument, literal >= 2V, empty clause, value code > 2 */
+  GSS_E_NOMEM = -2,     /* device allocation failed or the memory budget is exhausted */
+  GSS_E_CUDA = -3,      /* a CUDA runtime call failed (message in gss_last_error) */
+  GSS_E_OVERFLOW = -4,  /* more report records than the buffer given (count still returned) */
+  GSS_E_TIMEOUT = -5,   /* a bounded device-side wait gave up */
+  GSS_E_BUSY = -6,      /* no free slot (serving admission) */
+  GSS_E_STATE = -7      /* call out of order (e.g. gss_test before gss_set_assignments) */
+};
+
+enum { GSS_MODE_ALLF = 0, GSS_MODE_TRIGGER = 1 };
+
+#define GSS_MAX_ASSIGNMENTS 4096u /* largest N per assignment set */
+#define GSS_HEAD_WIDTH 8u         /* literals per clause kept in the head array */
+
+typedef struct gss_ctx gss_ctx;
+
+/* Context configuration; gss_config_init() fills the defaults. */
+typedef struct {
+  int device;                /* CUDA device ordinal (default 0) */
+  void* stream;              /* cudaStream_t to queue work on; NULL: the context creates one */
+  uint64_t report_capacity;  /* report records the device buffer holds (default 1 << 22) */
+  uint32_t max_assignments;  /* upper bound on N, <= GSS_MAX_ASSIGNMENTS (default 1024) */
+  uint32_t mode;             /* GSS_MODE_ALLF (default) or GSS_MODE_TRIGGER */
+  uint64_t mem_budget_bytes; /* cap on device bytes the context may hold; 0 = no cap */
+} gss_config;
+
+/*
+ * One report record: clause `clause_id` passes the test on assignment
+ * 32 * word + j for every bit j set in `mask` (never 0).  This is the
+ * report(i, mask) record of Listing multiTrigger (Section 4.3) with i the
+ * 32-assignment word.  Record order is unspecified.
+ */
+typedef struct {
+  uint32_t clause_id;
+  uint32_t word;
+  uint32_t mask;
+} gss_report;
+
+/* Context statistics (host-side counters, no synchronisation). */
+typedef struct {
+  uint32_t n_vars;
+  uint32_t n_assign;        /* N of the current assignment set (0 if none) */
+  uint64_t n_clauses;
+  uint64_t n_lits;
+  uint64_t device_bytes;    /* device memory held by the context */
+  uint64_t report_capacity;
+  uint64_t tests_run;       /* gss_test calls completed */
+  uint64_t pair_tests;      /* sum over gss_test calls of n_clauses * N */
+} gss_stats;
+
+/* ------------------------------------------------------------ lifecycle */
+
+/* Fill *cfg with the defaults listed in gss_config.  Returns GSS_E_INVAL if cfg is NULL. */
+int gss_config_init(gss_config* cfg);
+
+/*
+ * Create a context for V = n_vars variables (1 <= V < 2^31) on cfg->device.
+ * cfg may be NULL (defaults).  On success *out owns the device state.
+ * Errors: GSS_E_INVAL (bad V, bad config), GSS_E_CUDA (no device / bad
+ * stream), GSS_E_NOMEM.
+ */
+int gss_create(gss_ctx** out, uint32_t n_vars, const gss_config* cfg);
+
+/* Release every device and host resource of ctx (waits for its queued work). NULL is a no-op. */
+int gss_destroy(gss_ctx* ctx);
+
+/* ------------------------------------------------------------- clauses */
+
+/*
+ * Append n_clauses clauses to the resident database (Section 3.6: every
+ * learned clause is exported to the GPU, which keeps all of them).
+ *   offsets  host, n_clauses + 1 entries, offsets[0] = 0, strictly
+ *            increasing: clause i is lits[offsets[i] .. offsets[i+1]).
+ *   lits     host, offsets[n_clauses] literals, each l = 2v + s < 2V.
+ *   first_id out (nullable): id of the first new clause; the others follow.
+ * All or nothing: on GSS_E_INVAL (empty clause, literal >= 2V, offsets[0]
+ * != 0) or GSS_E_NOMEM the database is unchanged.  Synchronises the stream
+ * (validation result).  Duplicate literals are allowed; a clause holding
+ * l and not l is accepted and is never reported.
+ */
+int gss_add_clauses(gss_ctx* ctx, const uint64_t* offsets, uint64_t n_clauses, const uint32_t* lits,
+                    uint32_t* first_id);
+
+/* --------------------------------------------------------- assignments */
+
+/*
+ * Replace the assignment set by N = n_assign assignments (Section 3.4: each
+ * variable's values over the N assignments are packed into bit-words; here
+ * one false-plane row per literal, bit a set iff A_a(l) = F, plus one
+ * aggregate word per literal and 32-assignment group, Section 4.2).
+ *   values host, row-major [n_assign][n_vars] bytes, 0 = U, 1 = T, 2 = F.
+ * 0 <= n_assign <= cfg.max_assignments.  Assignments 32g .. 32g+31 form
+ * group g; grouping assignments of one solver thread together (Section 4.3)
+ * makes the group prefilter effective but never changes results.
+ * Queued on the stream (the host buffer is copied before return).  A value
+ * code above 2 is detected on the device and reported as GSS_E_INVAL by the
+ * next gss_fetch_reports / gss_report_count, with no records.
+ */
+int gss_set_assignments(gss_ctx* ctx, const uint8_t* values, uint32_t n_assign);
+
+/*
+ * As gss_set_assignments, but `d_values` is a DEVICE pointer on the
+ * context's device, rows `pitch` bytes apart (pitch >= n_vars).  The buffer
+ * must stay valid until the queued packing kernel has run.
+ */
+int gss_set_assignments_device(gss_ctx* ctx, const uint8_t* d_values, uint64_t pitch, uint32_t n_assign);
+
+/* ---------------------------------------------------------------- test */
+
+/*
+ * Test every resident clause against the current assignment set (Section
+ * 3.5: clauses in parallel, 32 assignments per word) and write report records
+ * to the context's device buffer, replacing those of the previous test.
+ * Queued on the stream; returns at once.  Errors: GSS_E_STATE (no assignment
+ * set), GSS_E_CUDA.
+ */
+int gss_test(gss_ctx* ctx);
+
+/*
+ * Wait for the last gss_test and copy its records to host buffer `out`
+ * (capacity `cap` records; out may be NULL when cap is 0).  *n_out receives
+ * the total number of records the test produced.  Returns GSS_E_OVERFLOW if
+ * that number exceeds cap (min(cap, n) records written) or the device buffer
+ * (the test must then be re-run after gss_set_report_capacity), GSS_E_INVAL
+ * if the assignment set held a bad value code, GSS_E_STATE if no test ran.
+ */
+int gss_fetch_reports(gss_ctx* ctx, gss_report* out, uint64_t cap, uint64_t* n_out);
+
+/*
+ * As gss_fetch_reports but copies nothing: waits for the last test and
+ * returns its record count.  The records stay in device memory, readable
+ * through gss_reports_device().
+ */
+int gss_report_count(gss_ctx* ctx, uint64_t* n_out);
+
+/* Device address of the context's report buffer (valid until the next capacity change or gss_destroy). */
+int gss_reports_device(gss_ctx* ctx, const gss_report** d_records, uint64_t* capacity);
+
+/* Resize the device report buffer to `cap` records (discards current records). */
+int gss_set_report_capacity(gss_ctx* ctx, uint64_t cap);
+
+/* Select GSS_MODE_ALLF or GSS_MODE_TRIGGER for the following gss_test calls. */
+int gss_set_mode(gss_ctx* ctx, uint32_t mode);
+
+/* ---------------------------------------------------------- diagnostics */
+
+int gss_get_stats(const gss_ctx* ctx, gss_stats* out);
+
+/* Message of the last failed call on ctx ("" if none); a static string for NULL ctx. */
+const char* gss_last_error(const gss_ctx* ctx);
+
+/* Name of a status code. */
+const char* gss_strerror(int code);
+
+/* Library version, (major << 16) | minor. */
+uint32_t gss_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSS_H */

@@ -1,0 +1,295 @@
+"""GB300 clause x assignment tests (GpuShareSat's data-parallel path, arXiv 2012.03119).
+
+Thin Python binding of the C ABI in ``include/gss.h`` (``libgss.so``, built in-tree
+for sm_103a).  Functions keep the C names; ``Context`` wraps a ``gss_ctx*``.  The
+binding only marshals arguments: every step of the path (clause ingest, packing,
+testing, report compaction) runs in the library's CUDA kernels.  There is no CPU
+fallback: importing fails loudly if the library is missing.
+
+Inputs may be numpy arrays (host) or torch tensors (host or CUDA); torch is used
+only for device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["Context", "GssError", "REPORT_DTYPE", "expand_reports", "load", "GSS_MODE_ALLF", "GSS_MODE_TRIGGER"]
+
+GSS_OK, GSS_E_INVAL, GSS_E_NOMEM, GSS_E_CUDA, GSS_E_OVERFLOW, GSS_E_TIMEOUT, GSS_E_BUSY, GSS_E_STATE = \
+    0, -1, -2, -3, -4, -5, -6, -7
+GSS_MODE_ALLF, GSS_MODE_TRIGGER = 0, 1
+GSS_MAX_ASSIGNMENTS = 4096
+GSS_HEAD_WIDTH = 8
+
+REPORT_DTYPE = np.dtype([("clause_id", "<u4"), ("word", "<u4"), ("mask", "<u4")])
+
+
+class gss_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("report_capacity", ctypes.c_uint64),
+                ("max_assignments", ctypes.c_uint32), ("mode", ctypes.c_uint32),
+                ("mem_budget_bytes", ctypes.c_uint64)]
+
+
+class gss_stats(ctypes.Structure):
+    _fields_ = [("n_vars", ctypes.c_uint32), ("n_assign", ctypes.c_uint32), ("n_clauses", ctypes.c_uint64),
+                ("n_lits", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64), ("report_capacity", ctypes.c_uint64),
+                ("tests_run", ctypes.c_uint64), ("pair_tests", ctypes.c_uint64)]
+
+
+class GssError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STRERR.get(code, code)}: {msg}")
+        self.code = code
+
+
+_STRERR = {0: "GSS_OK", -1: "GSS_E_INVAL", -2: "GSS_E_NOMEM", -3: "GSS_E_CUDA", -4: "GSS_E_OVERFLOW",
+           -5: "GSS_E_TIMEOUT", -6: "GSS_E_BUSY", -7: "GSS_E_STATE"}
+
+_lib = None
+
+# (name, restype, argtypes) of every entry point declared in include/gss.h
+P, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+SIGNATURES = {
+    "gss_config_init": (i32, [P]),
+    "gss_create": (i32, [P, u32, P]),
+    "gss_destroy": (i32, [P]),
+    "gss_add_clauses": (i32, [P, P, u64, P, P]),
+    "gss_set_assignments": (i32, [P, P, u32]),
+    "gss_set_assignments_device": (i32, [P, P, u64, u32]),
+    "gss_test": (i32, [P]),
+    "gss_fetch_reports": (i32, [P, P, u64, P]),
+    "gss_report_count": (i32, [P, P]),
+    "gss_reports_device": (i32, [P, P, P]),
+    "gss_set_report_capacity": (i32, [P, u64]),
+    "gss_set_mode": (i32, [P, u32]),
+    "gss_get_stats": (i32, [P, P]),
+    "gss_last_error": (ctypes.c_char_p, [P]),
+    "gss_strerror": (ctypes.c_char_p, [i32]),
+    "gss_version": (u32, []),
+}
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libgss.so (in-tree).  Raises ImportError when it is not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"{_build.LIB} is not built; run __graft_entry__.build() (nvcc, sm_103a)")
+    lib = ctypes.CDLL(_build.LIB)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(ctx_ptr, rc: int):
+    if rc != GSS_OK:
+        msg = load().gss_last_error(ctx_ptr)
+        raise GssError(rc, msg.decode() if msg else "")
+
+
+def _host_or_dev(a, dtype):
+    """Return (pointer, keepalive, is_device) for a numpy array or torch tensor."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            assert a.is_contiguous(), "tensor must be contiguous"
+            return ctypes.c_void_p(a.data_ptr()), a, a.is_cuda
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return ctypes.c_void_p(arr.ctypes.data), arr, False
+
+
+# ---------------------------------------------------------------- C-named wrappers
+def gss_config_init() -> gss_config:
+    cfg = gss_config()
+    load().gss_config_init(ctypes.byref(cfg))
+    return cfg
+
+
+def gss_create(n_vars: int, cfg: gss_config | None = None) -> ctypes.c_void_p:
+    out = ctypes.c_void_p()
+    rc = load().gss_create(ctypes.byref(out), n_vars, ctypes.byref(cfg) if cfg is not None else None)
+    if rc != GSS_OK:
+        raise GssError(rc, "gss_create failed")
+    return out
+
+
+def gss_destroy(ctx) -> None:
+    load().gss_destroy(ctx)
+
+
+def gss_add_clauses(ctx, offsets, lits) -> int:
+    off = np.ascontiguousarray(offsets, dtype=np.uint64)
+    lt = np.ascontiguousarray(lits, dtype=np.uint32)
+    first = ctypes.c_uint32()
+    n = len(off) - 1
+    _check(ctx, load().gss_add_clauses(ctx, ctypes.c_void_p(off.ctypes.data), n, ctypes.c_void_p(lt.ctypes.data),
+                                       ctypes.byref(first)))
+    return first.value
+
+
+def gss_set_assignments(ctx, values) -> None:
+    ptr, keep, dev = _host_or_dev(values, np.uint8)
+    n = keep.shape[0] if keep.ndim == 2 else 0
+    if dev:
+        pitch = keep.stride(0) * keep.element_size()
+        _check(ctx, load().gss_set_assignments_device(ctx, ptr, pitch, n))
+    else:
+        _check(ctx, load().gss_set_assignments(ctx, ptr, n))
+
+
+def gss_set_assignments_device(ctx, d_ptr: int, pitch: int, n_assign: int) -> None:
+    _check(ctx, load().gss_set_assignments_device(ctx, ctypes.c_void_p(d_ptr), pitch, n_assign))
+
+
+def gss_test(ctx) -> None:
+    _check(ctx, load().gss_test(ctx))
+
+
+def gss_report_count(ctx) -> int:
+    n = ctypes.c_uint64()
+    _check(ctx, load().gss_report_count(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def gss_fetch_reports(ctx, out: np.ndarray | None = None) -> np.ndarray:
+    """Wait for the last test and return its records (numpy REPORT_DTYPE).  ``out`` may be a
+    preallocated buffer (e.g. a numpy view of pinned memory) large enough for every record."""
+    lib = load()
+    n = ctypes.c_uint64()
+    if out is None:
+        rc = lib.gss_fetch_reports(ctx, None, 0, ctypes.byref(n))  # count only
+        if rc not in (GSS_OK, GSS_E_OVERFLOW):
+            _check(ctx, rc)
+        out = np.empty(n.value, dtype=REPORT_DTYPE)
+    assert out.dtype == REPORT_DTYPE and out.flags["C_CONTIGUOUS"]
+    _check(ctx, lib.gss_fetch_reports(ctx, ctypes.c_void_p(out.ctypes.data), len(out), ctypes.byref(n)))
+    return out[: n.value]
+
+
+def gss_set_report_capacity(ctx, cap: int) -> None:
+    _check(ctx, load().gss_set_report_capacity(ctx, cap))
+
+
+def gss_set_mode(ctx, mode: int) -> None:
+    _check(ctx, load().gss_set_mode(ctx, mode))
+
+
+def gss_get_stats(ctx) -> dict:
+    s = gss_stats()
+    _check(ctx, load().gss_get_stats(ctx, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in s._fields_}
+
+
+def gss_reports_device(ctx) -> tuple[int, int]:
+    p = ctypes.c_void_p()
+    cap = ctypes.c_uint64()
+    _check(ctx, load().gss_reports_device(ctx, ctypes.byref(p), ctypes.byref(cap)))
+    return p.value or 0, cap.value
+
+
+def gss_strerror(code: int) -> str:
+    return load().gss_strerror(code).decode()
+
+
+def gss_version() -> int:
+    return load().gss_version()
+
+
+# ---------------------------------------------------------------- object API
+class Context:
+    """Owns one ``gss_ctx``: a resident clause database, one assignment set and a report buffer."""
+
+    def __init__(self, n_vars: int, device: int = 0, stream=None, report_capacity: int = 1 << 22,
+                 max_assignments: int = 1024, mode: int = GSS_MODE_ALLF, mem_budget_bytes: int = 0):
+        cfg = gss_config_init()
+        cfg.device = device
+        cfg.stream = ctypes.c_void_p(_stream_handle(stream)) if stream is not None else None
+        cfg.report_capacity = report_capacity
+        cfg.max_assignments = max_assignments
+        cfg.mode = mode
+        cfg.mem_budget_bytes = mem_budget_bytes
+        self.n_vars = n_vars
+        self._stream = stream
+        self.ptr = gss_create(n_vars, cfg)
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            gss_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def add_clauses(self, offsets, lits) -> int:
+        return gss_add_clauses(self.ptr, offsets, lits)
+
+    def set_assignments(self, values) -> None:
+        gss_set_assignments(self.ptr, values)
+
+    def test(self) -> None:
+        gss_test(self.ptr)
+
+    def report_count(self) -> int:
+        return gss_report_count(self.ptr)
+
+    def fetch_reports(self, out=None) -> np.ndarray:
+        return gss_fetch_reports(self.ptr, out)
+
+    def set_report_capacity(self, cap: int) -> None:
+        gss_set_report_capacity(self.ptr, cap)
+
+    def set_mode(self, mode: int) -> None:
+        gss_set_mode(self.ptr, mode)
+
+    def stats(self) -> dict:
+        return gss_get_stats(self.ptr)
+
+    def run(self, values) -> np.ndarray:
+        """set_assignments + test + fetch_reports."""
+        self.set_assignments(values)
+        self.test()
+        return self.fetch_reports()
+
+
+def _stream_handle(stream) -> int:
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def expand_reports(rec: np.ndarray) -> np.ndarray:
+    """Records -> (clause, assignment) pairs sorted by clause then assignment (uint32 [R, 2])."""
+    rec = np.asarray(rec)
+    if len(rec) == 0:
+        return np.zeros((0, 2), np.uint32)
+    bits = np.unpackbits(rec["mask"].astype("<u4").view(np.uint8).reshape(-1, 4), axis=1, bitorder="little")
+    r, j = np.nonzero(bits)
+    c = rec["clause_id"][r].astype(np.uint64)
+    a = rec["word"][r].astype(np.uint64) * 32 + j.astype(np.uint64)
+    key = np.sort((c << np.uint64(32)) | a)
+    out = np.empty((len(key), 2), np.uint32)
+    out[:, 0] = (key >> np.uint64(32)).astype(np.uint32)
+    out[:, 1] = (key & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    return out

@@ -1,0 +1,489 @@
+// gss_abi.cu -- host implementation of the C ABI declared in include/gss.h.
+//
+// Owns the context: device buffers (clause database, assignment planes, report
+// buffer, status words), the stream, validation and error reporting.  Every step
+// of the tested path runs in the kernels of k_ingest.cu, k_pack.cu and k_test.cu;
+// this file only sizes buffers, copies host data in and out, and launches.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <unordered_map>
+
+#include "gss_internal.h"
+
+using namespace gss;
+
+struct gss_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  uint32_t V = 0, max_N = 0, mode = GSS_MODE_ALLF;
+  uint64_t budget = 0, bytes = 0;
+  int n_sms = 1;
+  std::unordered_map<void*, uint64_t> allocs;
+
+  // clause database
+  uint64_t m = 0, L = 0, cap_m = 0, cap_head = 0, cap_L = 0, cap_boff = 0;
+  uint64_t* off = nullptr;
+  uint32_t* lits = nullptr;
+  uint32_t* head = nullptr;
+  uint64_t* boff = nullptr;
+
+  // assignment set
+  uint32_t N = 0, Wp = 4, AWp = 1;
+  bool have_assign = false;
+  uint64_t Vp = 0;
+  uint8_t* codes = nullptr;
+  uint64_t codes_rows = 0;
+  uint32_t* P = nullptr;
+  uint32_t* aggF = nullptr;
+  uint32_t* aggU = nullptr;
+
+  // reports
+  gss_report* rec = nullptr;
+  uint64_t rec_cap = 0;
+  DevStatus* st = nullptr;    // [0]: pack + test, [1]: ingest
+  DevStatus* h_st = nullptr;  // pinned mirror
+  bool tested = false;
+  int grid[2][5] = {{0}};     // cached persistent grid per (mode, AWp)
+
+  uint64_t tests_run = 0, pair_tests = 0;
+  std::string err;
+};
+
+namespace {
+
+std::atomic<long> g_alloc_counter{0};
+
+int fail(gss_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+#define CK(ctx, call)                                                                         \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return fail((ctx), GSS_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int d) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != d) changed = cudaSetDevice(d) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (changed && prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// Host-side fault injection for tests: GSS_FAULT_ALLOC_AT=n fails the n-th device
+// allocation of the process (1-based) with GSS_E_NOMEM; no GPU fault is involved.
+bool injected_alloc_failure() {
+  const char* s = getenv("GSS_FAULT_ALLOC_AT");
+  long n = g_alloc_counter.fetch_add(1) + 1;
+  return s && *s && atol(s) == n;
+}
+
+int dev_alloc(gss_ctx* c, void** p, uint64_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 256;
+  if (injected_alloc_failure()) return fail(c, GSS_E_NOMEM, "injected allocation failure (%llu bytes)",
+                                            (unsigned long long)bytes);
+  if (c->budget && c->bytes + bytes > c->budget)
+    return fail(c, GSS_E_NOMEM, "memory budget exceeded: %llu + %llu > %llu bytes", (unsigned long long)c->bytes,
+                (unsigned long long)bytes, (unsigned long long)c->budget);
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(c, GSS_E_NOMEM, "cudaMalloc(%llu): %s", (unsigned long long)bytes, cudaGetErrorString(e));
+  }
+  c->bytes += bytes;
+  c->allocs[*p] = bytes;
+  return GSS_OK;
+}
+
+void dev_free(gss_ctx* c, void* p) {
+  if (!p) return;
+  auto it = c->allocs.find(p);
+  if (it != c->allocs.end()) {
+    c->bytes -= it->second;
+    c->allocs.erase(it);
+  }
+  cudaFree(p);
+}
+
+// Grow a device array to hold `need` elements, preserving the first `used`.
+template <class T>
+int grow(gss_ctx* c, T*& ptr, uint64_t& cap, uint64_t used, uint64_t need) {
+  if (need <= cap && ptr) return GSS_OK;
+  uint64_t ncap = cap + cap / 2;
+  if (ncap < need) ncap = need;
+  if (ncap < 1024) ncap = 1024;
+  void* np = nullptr;
+  int rc = dev_alloc(c, &np, ncap * sizeof(T));
+  if (rc) return rc;
+  if (ptr && used) {
+    cudaError_t e = cudaMemcpyAsync(np, ptr, used * sizeof(T), cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      dev_free(c, np);
+      return fail(c, GSS_E_CUDA, "grow copy: %s", cudaGetErrorString(e));
+    }
+  }
+  dev_free(c, ptr);
+  ptr = static_cast<T*>(np);
+  cap = ncap;
+  return GSS_OK;
+}
+
+uint32_t words_stride(uint32_t N) {  // plane row stride in 32-bit words: a power of two >= 4
+  const uint32_t W = (N + 31) / 32;
+  uint32_t p = 4;
+  while (p < W) p <<= 1;
+  return p;
+}
+
+uint32_t agg_stride(uint32_t Wp) { return Wp <= 32 ? 1 : Wp / 32; }  // 1, 2 or 4 words
+
+int ensure_planes(gss_ctx* c) {
+  if (c->P) return GSS_OK;
+  const uint32_t Wp = words_stride(c->max_N), AWp = agg_stride(Wp);
+  int rc;
+  void* p;
+  if ((rc = dev_alloc(c, &p, (2ull * c->V + 2) * Wp * 4))) return rc;
+  c->P = static_cast<uint32_t*>(p);
+  if ((rc = dev_alloc(c, &p, (2ull * c->V + 2) * AWp * 4))) return rc;
+  c->aggF = static_cast<uint32_t*>(p);
+  if ((rc = dev_alloc(c, &p, (c->V + 1ull) * AWp * 4))) return rc;
+  c->aggU = static_cast<uint32_t*>(p);
+  return GSS_OK;
+}
+
+int sync_status(gss_ctx* c) {
+  CK(c, cudaMemcpyAsync(c->h_st, c->st, 2 * sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return GSS_OK;
+}
+
+int launch_grid(gss_ctx* c, int mode, uint32_t AWp) {
+  int& g = c->grid[mode][AWp];
+  if (!g) g = test_grid_size(mode, AWp, c->n_sms);
+  return g;
+}
+
+void release(gss_ctx* c) {
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  while (!c->allocs.empty()) dev_free(c, c->allocs.begin()->first);
+  if (c->h_st) cudaFreeHost(c->h_st);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+int gss_config_init(gss_config* cfg) {
+  if (!cfg) return GSS_E_INVAL;
+  memset(cfg, 0, sizeof *cfg);
+  cfg->device = 0;
+  cfg->stream = nullptr;
+  cfg->report_capacity = 1ull << 22;
+  cfg->max_assignments = 1024;
+  cfg->mode = GSS_MODE_ALLF;
+  cfg->mem_budget_bytes = 0;
+  return GSS_OK;
+}
+
+int gss_create(gss_ctx** out, uint32_t n_vars, const gss_config* cfg_in) {
+  if (!out) return GSS_E_INVAL;
+  *out = nullptr;
+  gss_config cfg;
+  if (cfg_in) cfg = *cfg_in; else gss_config_init(&cfg);
+  if (n_vars == 0 || n_vars >= (1u << 31)) return GSS_E_INVAL;
+  if (cfg.max_assignments == 0 || cfg.max_assignments > GSS_MAX_ASSIGNMENTS) return GSS_E_INVAL;
+  if (cfg.mode != GSS_MODE_ALLF && cfg.mode != GSS_MODE_TRIGGER) return GSS_E_INVAL;
+  int n_dev = 0;
+  if (cudaGetDeviceCount(&n_dev) != cudaSuccess || cfg.device < 0 || cfg.device >= n_dev) {
+    cudaGetLastError();
+    return GSS_E_CUDA;
+  }
+  gss_ctx* c = new (std::nothrow) gss_ctx();
+  if (!c) return GSS_E_NOMEM;
+  DeviceGuard dg(cfg.device);
+  c->device = cfg.device;
+  c->V = n_vars;
+  c->max_N = cfg.max_assignments;
+  c->mode = cfg.mode;
+  c->budget = cfg.mem_budget_bytes;
+  c->Vp = (n_vars + 15ull) / 16 * 16;
+  int rc = GSS_OK;
+  if (cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) c->n_sms = 1;
+  if (cfg.stream) {
+    c->stream = static_cast<cudaStream_t>(cfg.stream);
+  } else if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    return GSS_E_CUDA;
+  } else {
+    c->own_stream = true;
+  }
+  void* p = nullptr;
+  if (cudaMallocHost(&p, 2 * sizeof(DevStatus)) != cudaSuccess) rc = GSS_E_NOMEM;
+  c->h_st = static_cast<DevStatus*>(p);
+  if (!rc) rc = dev_alloc(c, &p, 2 * sizeof(DevStatus));
+  if (!rc) {
+    c->st = static_cast<DevStatus*>(p);
+    if (cudaMemsetAsync(c->st, 0, 2 * sizeof(DevStatus), c->stream) != cudaSuccess) rc = GSS_E_CUDA;
+  }
+  if (!rc) {
+    c->rec_cap = cfg.report_capacity ? cfg.report_capacity : 1;
+    rc = dev_alloc(c, &p, c->rec_cap * sizeof(gss_report));
+    c->rec = static_cast<gss_report*>(p);
+  }
+  if (!rc) {
+    rc = grow(c, c->off, c->cap_m, 0, 1025);
+    if (!rc && cudaMemsetAsync(c->off, 0, sizeof(uint64_t), c->stream) != cudaSuccess) rc = GSS_E_CUDA;
+  }
+  if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = GSS_E_CUDA;
+  if (rc) {
+    release(c);
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return GSS_OK;
+}
+
+int gss_destroy(gss_ctx* c) {
+  if (!c) return GSS_OK;
+  DeviceGuard dg(c->device);
+  release(c);
+  delete c;
+  return GSS_OK;
+}
+
+int gss_add_clauses(gss_ctx* c, const uint64_t* offsets, uint64_t n, const uint32_t* lits, uint32_t* first_id) {
+  if (!c) return GSS_E_INVAL;
+  c->err.clear();
+  if (n == 0) {
+    if (first_id) *first_id = (uint32_t)c->m;
+    return GSS_OK;
+  }
+  if (!offsets) return fail(c, GSS_E_INVAL, "offsets is NULL");
+  if (offsets[0] != 0) return fail(c, GSS_E_INVAL, "offsets[0] must be 0");
+  const uint64_t L = offsets[n];
+  if (L && !lits) return fail(c, GSS_E_INVAL, "lits is NULL");
+  if (c->m + n >= (1ull << 32)) return fail(c, GSS_E_INVAL, "more than 2^32 - 1 clauses");
+  DeviceGuard dg(c->device);
+  int rc;
+  // cap_m counts offsets entries (m + 1); cap_head counts head literals (m * HEAD_K)
+  if ((rc = grow(c, c->off, c->cap_m, c->m + 1, c->m + n + 1))) return rc;
+  if ((rc = grow(c, c->head, c->cap_head, c->m * HEAD_K, (c->m + n) * HEAD_K))) return rc;
+  if ((rc = grow(c, c->lits, c->cap_L, c->L, c->L + L))) return rc;
+  if ((rc = grow(c, c->boff, c->cap_boff, 0, n + 1))) return rc;
+  CK(c, cudaMemsetAsync(c->st + 1, 0, sizeof(DevStatus), c->stream));
+  CK(c, cudaMemcpyAsync(c->boff, offsets, (n + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, c->stream));
+  if (L) CK(c, cudaMemcpyAsync(c->lits + c->L, lits, L * sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream));
+  CK(c, launch_ingest(c->boff, n, L, c->L, c->off + c->m, c->head + c->m * HEAD_K, c->lits, c->V, c->st + 1,
+                      c->stream));
+  if ((rc = sync_status(c))) return rc;
+  if (c->h_st[1].bad_size) return fail(c, GSS_E_INVAL, "empty clause or offsets not increasing / past the batch");
+  if (c->h_st[1].bad_lit) return fail(c, GSS_E_INVAL, "literal >= 2 * n_vars (%u)", 2 * c->V);
+  if (first_id) *first_id = (uint32_t)c->m;
+  c->m += n;
+  c->L += L;
+  return GSS_OK;
+}
+
+static int set_assignments_common(gss_ctx* c, const uint8_t* src, uint64_t pitch, uint32_t n, bool device_src) {
+  if (!c) return GSS_E_INVAL;
+  c->err.clear();
+  if (n > c->max_N) return fail(c, GSS_E_INVAL, "n_assign %u > max_assignments %u", n, c->max_N);
+  if (n && !src) return fail(c, GSS_E_INVAL, "values is NULL");
+  if (device_src && pitch < c->V) return fail(c, GSS_E_INVAL, "pitch %llu < n_vars %u", (unsigned long long)pitch, c->V);
+  DeviceGuard dg(c->device);
+  int rc;
+  if ((rc = ensure_planes(c))) return rc;
+  c->have_assign = false;
+  c->tested = false;
+  CK(c, cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream));
+  const uint32_t Wp = words_stride(n ? n : 1);
+  const uint32_t AWp = agg_stride(Wp);
+  const uint8_t* codes = src;
+  uint64_t cpitch = pitch;
+  const bool aligned = device_src && pitch % 4 == 0 && (reinterpret_cast<uintptr_t>(src) % 4) == 0;
+  if (n && !aligned) {  // host data, or a device layout the packing kernel cannot read as 32-bit words
+    if (c->codes_rows < n) {
+      dev_free(c, c->codes);
+      c->codes = nullptr;
+      c->codes_rows = 0;
+      void* p;
+      if ((rc = dev_alloc(c, &p, (uint64_t)c->max_N * c->Vp))) return rc;
+      c->codes = static_cast<uint8_t*>(p);
+      c->codes_rows = c->max_N;
+      CK(c, cudaMemsetAsync(c->codes, 0, (uint64_t)c->max_N * c->Vp, c->stream));  // padding columns stay U
+    }
+    CK(c, cudaMemcpy2DAsync(c->codes, c->Vp, src, device_src ? pitch : c->V, c->V, n,
+                            device_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    codes = c->codes;
+    cpitch = c->Vp;
+  }
+  if (n) CK(c, launch_pack(codes, cpitch, c->V, n, Wp, AWp, c->P, c->aggF, c->aggU, c->st, c->stream));
+  c->N = n;
+  c->Wp = Wp;
+  c->AWp = AWp;
+  c->have_assign = true;
+  return GSS_OK;
+}
+
+int gss_set_assignments(gss_ctx* c, const uint8_t* values, uint32_t n_assign) {
+  return set_assignments_common(c, values, 0, n_assign, false);
+}
+
+int gss_set_assignments_device(gss_ctx* c, const uint8_t* d_values, uint64_t pitch, uint32_t n_assign) {
+  return set_assignments_common(c, d_values, pitch, n_assign, true);
+}
+
+int gss_test(gss_ctx* c) {
+  if (!c) return GSS_E_INVAL;
+  c->err.clear();
+  if (!c->have_assign) return fail(c, GSS_E_STATE, "gss_test before gss_set_assignments");
+  DeviceGuard dg(c->device);
+  CK(c, cudaMemsetAsync(&c->st->n_records, 0, sizeof(unsigned long long), c->stream));
+  if (c->m && c->N) {
+    ClauseView db{c->off, c->lits, c->head, 2u * c->V};
+    PlaneView pv{c->P, c->aggF, c->aggU, c->Wp, c->AWp, c->N};
+    CK(c, launch_test((int)c->mode, db, 0, c->m, pv, c->rec, c->rec_cap, c->st, launch_grid(c, c->mode, c->AWp),
+                      c->stream));
+  }
+  c->tested = true;
+  c->tests_run += 1;
+  c->pair_tests += c->m * (uint64_t)c->N;
+  return GSS_OK;
+}
+
+static int wait_test(gss_ctx* c, uint64_t* n) {
+  if (!c->tested) return fail(c, GSS_E_STATE, "no gss_test to fetch");
+  int rc = sync_status(c);
+  if (rc) return rc;
+  if (c->h_st[0].bad_code) {
+    *n = 0;
+    return fail(c, GSS_E_INVAL, "assignment value code outside {0 = U, 1 = T, 2 = F}");
+  }
+  *n = c->h_st[0].n_records;
+  return GSS_OK;
+}
+
+int gss_fetch_reports(gss_ctx* c, gss_report* out, uint64_t cap, uint64_t* n_out) {
+  if (!c || (cap && !out)) return c ? fail(c, GSS_E_INVAL, "out is NULL") : GSS_E_INVAL;
+  c->err.clear();
+  DeviceGuard dg(c->device);
+  uint64_t n = 0;
+  int rc = wait_test(c, &n);
+  if (n_out) *n_out = n;
+  if (rc) return rc;
+  uint64_t k = n < cap ? n : cap;
+  if (k > c->rec_cap) k = c->rec_cap;
+  if (k) {
+    CK(c, cudaMemcpyAsync(out, c->rec, k * sizeof(gss_report), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+  }
+  if (n > c->rec_cap)
+    return fail(c, GSS_E_OVERFLOW, "device report buffer overflowed: %llu records > capacity %llu; "
+                "raise it with gss_set_report_capacity and re-run gss_test",
+                (unsigned long long)n, (unsigned long long)c->rec_cap);
+  if (n > cap)
+    return fail(c, GSS_E_OVERFLOW, "%llu records > caller capacity %llu", (unsigned long long)n,
+                (unsigned long long)cap);
+  return GSS_OK;
+}
+
+int gss_report_count(gss_ctx* c, uint64_t* n_out) {
+  if (!c || !n_out) return GSS_E_INVAL;
+  c->err.clear();
+  DeviceGuard dg(c->device);
+  int rc = wait_test(c, n_out);
+  if (rc) return rc;
+  if (*n_out > c->rec_cap)
+    return fail(c, GSS_E_OVERFLOW, "device report buffer overflowed: %llu records > capacity %llu",
+                (unsigned long long)*n_out, (unsigned long long)c->rec_cap);
+  return GSS_OK;
+}
+
+int gss_reports_device(gss_ctx* c, const gss_report** d_records, uint64_t* capacity) {
+  if (!c || !d_records) return GSS_E_INVAL;
+  *d_records = c->rec;
+  if (capacity) *capacity = c->rec_cap;
+  return GSS_OK;
+}
+
+int gss_set_report_capacity(gss_ctx* c, uint64_t cap) {
+  if (!c || cap == 0) return c ? fail(c, GSS_E_INVAL, "capacity must be > 0") : GSS_E_INVAL;
+  c->err.clear();
+  DeviceGuard dg(c->device);
+  CK(c, cudaStreamSynchronize(c->stream));
+  void* p = nullptr;
+  int rc = dev_alloc(c, &p, cap * sizeof(gss_report));
+  if (rc) return rc;
+  dev_free(c, c->rec);
+  c->rec = static_cast<gss_report*>(p);
+  c->rec_cap = cap;
+  c->tested = false;
+  return GSS_OK;
+}
+
+int gss_set_mode(gss_ctx* c, uint32_t mode) {
+  if (!c) return GSS_E_INVAL;
+  if (mode != GSS_MODE_ALLF && mode != GSS_MODE_TRIGGER) return fail(c, GSS_E_INVAL, "unknown mode %u", mode);
+  c->mode = mode;
+  return GSS_OK;
+}
+
+int gss_get_stats(const gss_ctx* c, gss_stats* o) {
+  if (!c || !o) return GSS_E_INVAL;
+  o->n_vars = c->V;
+  o->n_assign = c->have_assign ? c->N : 0;
+  o->n_clauses = c->m;
+  o->n_lits = c->L;
+  o->device_bytes = c->bytes;
+  o->report_capacity = c->rec_cap;
+  o->tests_run = c->tests_run;
+  o->pair_tests = c->pair_tests;
+  return GSS_OK;
+}
+
+const char* gss_last_error(const gss_ctx* c) {
+  if (!c) return "no context";
+  return c->err.c_str();
+}
+
+const char* gss_strerror(int code) {
+  switch (code) {
+    case GSS_OK: return "GSS_OK";
+    case GSS_E_INVAL: return "GSS_E_INVAL";
+    case GSS_E_NOMEM: return "GSS_E_NOMEM";
+    case GSS_E_CUDA: return "GSS_E_CUDA";
+    case GSS_E_OVERFLOW: return "GSS_E_OVERFLOW";
+    case GSS_E_TIMEOUT: return "GSS_E_TIMEOUT";
+    case GSS_E_BUSY: return "GSS_E_BUSY";
+    case GSS_E_STATE: return "GSS_E_STATE";
+    default: return "GSS_E_UNKNOWN";
+  }
+}
+
+uint32_t gss_version(void) { return (0u << 16) | 1u; }
+
+}  // extern "C"

@@ -1,0 +1,86 @@
+"""C-ABI library: builds for sm_103a, loads, exports every declared symbol (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2012_03119_gb300 as gss
+from paper_2012_03119_gb300 import _build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"^[A-Za-z_][\w\s\*]*?\b(gss_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return gss.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 16
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared but not exported"
+
+
+def test_binding_covers_every_symbol():
+    assert set(declared_functions()) <= set(gss.SIGNATURES)
+
+
+def test_exports_are_c_symbols(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", _build.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (gss_\w+)", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_cubin_targets_sm_103a(lib):
+    out = subprocess.run(["cuobjdump", "--list-elf", _build.LIB], capture_output=True, text=True).stdout
+    assert "sm_103a" in out
+
+
+def test_host_only_entry_points(lib):
+    assert gss.gss_strerror(-4) == "GSS_E_OVERFLOW"
+    assert gss.gss_strerror(0) == "GSS_OK"
+    cfg = gss.gss_config_init()
+    assert cfg.report_capacity == 1 << 22 and cfg.max_assignments == 1024 and cfg.mode == 0
+    assert lib.gss_config_init(None) == gss.GSS_E_INVAL
+    assert lib.gss_destroy(None) == 0
+    assert lib.gss_last_error(None) == b"no context"
+
+
+def test_create_argument_checks(lib):
+    out = ctypes.c_void_p()
+    assert lib.gss_create(None, 10, None) == gss.GSS_E_INVAL
+    assert lib.gss_create(ctypes.byref(out), 0, None) == gss.GSS_E_INVAL
+    cfg = gss.gss_config_init()
+    cfg.max_assignments = gss.GSS_MAX_ASSIGNMENTS + 1
+    assert lib.gss_create(ctypes.byref(out), 10, ctypes.byref(cfg)) == gss.GSS_E_INVAL
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    out = ctypes.c_void_p()
+    assert lib.gss_create(ctypes.byref(out), 10, None) == gss.GSS_E_CUDA
+    assert not out.value
+
+
+def test_expand_reports_host_helper():
+    import numpy as np
+    rec = np.zeros(2, gss.REPORT_DTYPE)
+    rec[0] = (5, 1, 0b101)
+    rec[1] = (2, 0, 1 << 31)
+    assert gss.expand_reports(rec).tolist() == [[2, 31], [5, 32], [5, 34]]
