@@ -54,7 +54,7 @@ enum {
 enum { GSS_MODE_ALLF = 0, GSS_MODE_TRIGGER = 1 };
 
 #define GSS_MAX_ASSIGNMENTS 4096u /* largest N per assignment set */
-#define GSS_HEAD_WIDTH 8u         /* literals per clause kept in the head array */
+#define GSS_HEAD_WIDTH 16u        /* literals per clause kept in the head planes */
 
 typedef struct gss_ctx gss_ctx;
 

@@ -24,7 +24,7 @@ GSS_OK, GSS_E_INVAL, GSS_E_NOMEM, GSS_E_CUDA, GSS_E_OVERFLOW, GSS_E_TIMEOUT, GSS
     0, -1, -2, -3, -4, -5, -6, -7
 GSS_MODE_ALLF, GSS_MODE_TRIGGER = 0, 1
 GSS_MAX_ASSIGNMENTS = 4096
-GSS_HEAD_WIDTH = 8
+GSS_HEAD_WIDTH = 16
 
 REPORT_DTYPE = np.dtype([("clause_id", "<u4"), ("word", "<u4"), ("mask", "<u4")])
 

@@ -29,10 +29,11 @@ struct gss_ctx {
   std::unordered_map<void*, uint64_t> allocs;
 
   // clause database
-  uint64_t m = 0, L = 0, cap_m = 0, cap_head = 0, cap_L = 0, cap_boff = 0;
+  uint64_t m = 0, L = 0, cap_m = 0, cap_head0 = 0, cap_head1 = 0, cap_L = 0, cap_boff = 0;
   uint64_t* off = nullptr;
   uint32_t* lits = nullptr;
-  uint32_t* head = nullptr;
+  uint32_t* head0 = nullptr;
+  uint32_t* head1 = nullptr;
   uint64_t* boff = nullptr;
 
   // assignment set
@@ -289,16 +290,17 @@ int gss_add_clauses(gss_ctx* c, const uint64_t* offsets, uint64_t n, const uint3
   if (c->m + n >= (1ull << 32)) return fail(c, GSS_E_INVAL, "more than 2^32 - 1 clauses");
   DeviceGuard dg(c->device);
   int rc;
-  // cap_m counts offsets entries (m + 1); cap_head counts head literals (m * HEAD_K)
+  // cap_m counts offsets entries (m + 1); head capacities count literals (8 per clause per plane)
   if ((rc = grow(c, c->off, c->cap_m, c->m + 1, c->m + n + 1))) return rc;
-  if ((rc = grow(c, c->head, c->cap_head, c->m * HEAD_K, (c->m + n) * HEAD_K))) return rc;
+  if ((rc = grow(c, c->head0, c->cap_head0, c->m * 8, (c->m + n) * 8))) return rc;
+  if ((rc = grow(c, c->head1, c->cap_head1, c->m * 8, (c->m + n) * 8))) return rc;
   if ((rc = grow(c, c->lits, c->cap_L, c->L, c->L + L))) return rc;
   if ((rc = grow(c, c->boff, c->cap_boff, 0, n + 1))) return rc;
   CK(c, cudaMemsetAsync(c->st + 1, 0, sizeof(DevStatus), c->stream));
   CK(c, cudaMemcpyAsync(c->boff, offsets, (n + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, c->stream));
   if (L) CK(c, cudaMemcpyAsync(c->lits + c->L, lits, L * sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream));
-  CK(c, launch_ingest(c->boff, n, L, c->L, c->off + c->m, c->head + c->m * HEAD_K, c->lits, c->V, c->st + 1,
-                      c->stream));
+  CK(c, launch_ingest(c->boff, n, L, c->L, c->off + c->m, c->head0 + c->m * 8, c->head1 + c->m * 8, c->lits, c->V,
+                      c->st + 1, c->stream));
   if ((rc = sync_status(c))) return rc;
   if (c->h_st[1].bad_size) return fail(c, GSS_E_INVAL, "empty clause or offsets not increasing / past the batch");
   if (c->h_st[1].bad_lit) return fail(c, GSS_E_INVAL, "literal >= 2 * n_vars (%u)", 2 * c->V);
@@ -364,7 +366,7 @@ int gss_test(gss_ctx* c) {
   DeviceGuard dg(c->device);
   CK(c, cudaMemsetAsync(&c->st->n_records, 0, sizeof(unsigned long long), c->stream));
   if (c->m && c->N) {
-    ClauseView db{c->off, c->lits, c->head, 2u * c->V};
+    ClauseView db{c->off, c->lits, c->head0, c->head1, 2u * c->V};
     PlaneView pv{c->P, c->aggF, c->aggU, c->Wp, c->AWp, c->N};
     CK(c, launch_test((int)c->mode, db, 0, c->m, pv, c->rec, c->rec_cap, c->st, launch_grid(c, c->mode, c->AWp),
                       c->stream));
@@ -382,6 +384,10 @@ static int wait_test(gss_ctx* c, uint64_t* n) {
   if (c->h_st[0].bad_code) {
     *n = 0;
     return fail(c, GSS_E_INVAL, "assignment value code outside {0 = U, 1 = T, 2 = F}");
+  }
+  if (c->h_st[0].timeout) {
+    *n = 0;
+    return fail(c, GSS_E_TIMEOUT, "a bounded device wait gave up; the records of this test are incomplete");
   }
   *n = c->h_st[0].n_records;
   return GSS_OK;

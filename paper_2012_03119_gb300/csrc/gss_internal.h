@@ -3,15 +3,16 @@
 // Device data layout (all resident in HBM, owned by the context):
 //   off    u64 [m + 1]           CSR offsets of the clause database (global literal index)
 //   lits   u32 [L]               literals, l = 2v + s
-//   head   u32 [m][HEAD_K]       first HEAD_K literals of each clause, padded with PAD = 2V
+//   head0  u32 [m][8]            literals 0..7 of each clause, padded with PAD = 2V
+//   head1  u32 [m][8]            literals 8..15 of each clause, padded with PAD
 //   P      u32 [2V + 2][Wp]      false planes: P[l][w] bit j set iff assignment 32w + j gives
 //                                literal l the value F (P[2v] = isFalse(v), P[2v+1] = isTrue(v));
 //                                rows 2V, 2V + 1 are all ones (PAD is neutral under AND)
 //   aggF   u32 [2V + 2][AWp]     group aggregate of P: bit g set iff P[l][g] != 0
 //                                ("F is in G(l)" for the 32-assignment group g, Section 4.2)
 //   aggU   u32 [V + 1][AWp]      bit g set iff some assignment of group g leaves v U (row V = 0)
-// W = ceil(N / 32) words, Wp = row stride (power of two >= 4 when W <= 32, else a
-// multiple of 32), AWp = Wp / 32 rounded up (1, 2 or 4).
+// W = ceil(N / 32) words, Wp = row stride (a power of two >= max(4, W)),
+// AWp = max(1, Wp / 32) (1, 2 or 4).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -20,8 +21,8 @@
 
 namespace gss {
 
-constexpr uint32_t HEAD_K = GSS_HEAD_WIDTH;
-static_assert(HEAD_K == 8, "kernels load the head as two uint4");
+constexpr uint32_t HEAD_K = GSS_HEAD_WIDTH;  // literals kept per clause outside the CSR (two planes of 8)
+static_assert(HEAD_K == 16, "kernels read the head as two planes of 8 literals");
 
 // Device-side status words, reset by the host between phases.
 struct DevStatus {
@@ -45,7 +46,8 @@ struct PlaneView {
 struct ClauseView {
   const uint64_t* off;
   const uint32_t* lits;
-  const uint32_t* head;
+  const uint32_t* head0;
+  const uint32_t* head1;
   uint32_t pad;  // PAD literal = 2V
 };
 
@@ -56,9 +58,10 @@ cudaError_t launch_pack(const uint8_t* codes, uint64_t pitch, uint32_t V, uint32
                         uint32_t* P, uint32_t* aggF, uint32_t* aggU, DevStatus* st, cudaStream_t s);
 
 // Ingest a batch: batch offsets (n + 1, batch-relative) -> db offsets at off_db[n0 + 1 ..],
-// heads for the new clauses, validation flags.  The batch literals are already at lits_db[L0 ..).
+// head planes for the new clauses, validation flags.  The batch literals are already at lits_db[L0 ..).
 cudaError_t launch_ingest(const uint64_t* boff, uint64_t n, uint64_t L, uint64_t L0, uint64_t* off_db_at_n0,
-                          uint32_t* head_at_n0, const uint32_t* lits_db, uint32_t V, DevStatus* st, cudaStream_t s);
+                          uint32_t* head0_at_n0, uint32_t* head1_at_n0, const uint32_t* lits_db, uint32_t V,
+                          DevStatus* st, cudaStream_t s);
 
 // Test clauses [c_lo, c_hi) against the planes; append records.
 cudaError_t launch_test(int mode, const ClauseView& db, uint64_t c_lo, uint64_t c_hi, const PlaneView& pv,

@@ -3,26 +3,32 @@
 // What is computed (per clause c, per assignment a):
 //   GSS_MODE_ALLF     every literal of c is F under a: c "would have been in conflict"
 //                     (Section 3.3); the allFalse recurrence of Listing assignmentTrigger
-//                     (Section 3.4), allFalse &= isFalse(l), over 32 assignments per word.
+//                     (Section 3.4), allFalse &= isFalse(l), 32 assignments per word.
 //   GSS_MODE_TRIGGER  Definition "triggers" (Section 3.3): the full recurrence of Listing
 //                     assignmentTrigger, oneUndef = (allFalse & U(l)) | (oneUndef & F(l)),
 //                     allFalse &= F(l), result allFalse | oneUndef.
 //
 // How (Sections 3.5 and 4.3, re-planned for GB300):
 //   * one lane per clause, 32 clauses per warp, persistent grid-stride over 32-clause tiles;
-//   * the clause's first 8 literals come from the head array: two 16-byte streaming loads
-//     per lane, 1 KiB contiguous per warp;
-//   * stage A is Listing multiTrigger's group test: the aggregate words (one bit per
-//     32-assignment group, Section 4.2) are ANDed (all-F) or run through the
-//     aggregateTrigger recurrence (trigger).  The aggregate rows are 4-16 bytes per literal
-//     and small enough (8 MiB at V = 1M) to stay in L2, the hottest ones in L1.  By the
-//     Theorem of Section 4.2 a group whose aggregate test is negative holds no hit;
-//   * literals past the head are read from the CSR only while some group is alive;
-//   * stage B runs the exact word recurrence on each surviving group (Listing
-//     multiTrigger's inner assignmentTrigger call) and appends one record per non-zero
-//     word with a warp ballot, a population count and one atomicAdd per warp
-//     (report(i, mask) of Listing multiTrigger).
-// Records past the buffer capacity are counted but not written.
+//   * the tile's head0 (literals 0..7 of its 32 clauses, 1 KiB) is brought into shared
+//     memory by a TMA bulk copy (cp.async.bulk + mbarrier), double-buffered: the copy of
+//     the warp's next tile is in flight while the current one is tested;
+//   * stage A is Listing multiTrigger's group test: per 32-assignment group one aggregate
+//     bit per literal (Section 4.2), ANDed (all-F) or run through the aggregateTrigger
+//     recurrence (trigger).  All gathers of a batch of literals are issued before they are
+//     combined, so a batch costs one L2 round trip.  Literals 8..15 come from head1 (one
+//     sector per clause, no offset lookup) and later ones from the CSR, only while some
+//     group is alive.  By the Theorem of Section 4.2 a group whose aggregate test fails
+//     holds no hit;
+//   * stage B is multiTrigger's inner assignmentTrigger call: the warp's surviving
+//     (clause, group) pairs are compacted into shared memory and each lane runs the exact
+//     word recurrence of one pair, again with a batch's gathers in flight together;
+//   * each non-zero word becomes one record {clause, word, mask} (report(i, mask) of
+//     Listing multiTrigger), appended with a ballot, a population count and one atomicAdd
+//     per warp.  Records past the capacity are counted but not written.
+//
+// The PAD literal 2V is neutral in both modes: its P and aggF rows are all ones and its
+// aggU row is zero, so padded head slots need no branch.
 #include "gss_internal.h"
 
 namespace gss {
@@ -30,6 +36,67 @@ namespace {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int TEST_THREADS = 256;
+constexpr int TEST_WARPS = TEST_THREADS / 32;
+constexpr uint32_t PAIR_CAP = 64;        // candidate pairs staged per warp per round
+constexpr uint64_t WAIT_NS = 1000000000; // bounded mbarrier wait: 1 s
+
+struct __align__(128) WarpSmem {
+  uint32_t ring[2][32 * 8];  // head0 of the current and the next tile
+  uint32_t pairs[PAIR_CAP];  // owner lane | group << 5
+  unsigned long long bar[2];
+};
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// Bulk copy global -> shared; both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for phase `parity` of the barrier; gives up after WAIT_NS and returns false.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (uint32_t i = 0; i < (1u << 28); ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63u) == 63u && globaltimer_ns() - t0 > WAIT_NS) return false;
+  }
+  return false;
+}
+
+// ------------------------------------------------------------------ math helpers
+__device__ __forceinline__ uint32_t valid_bits(uint32_t N, uint32_t w) {
+  const uint32_t lo = w * 32u;
+  if (lo >= N) return 0u;
+  const uint32_t rem = N - lo;
+  return rem >= 32u ? FULL : ((1u << rem) - 1u);
+}
 
 template <int AW>
 __device__ __forceinline__ void load_agg(const uint32_t* __restrict__ base, uint32_t row, uint32_t (&r)[AW]) {
@@ -45,72 +112,106 @@ __device__ __forceinline__ void load_agg(const uint32_t* __restrict__ base, uint
 }
 
 template <int AW>
-__device__ __forceinline__ bool any_bit(const uint32_t (&a)[AW]) {
+__device__ __forceinline__ bool any2(const uint32_t (&a)[AW], const uint32_t (&b)[AW]) {
   uint32_t o = 0;
 #pragma unroll
-  for (int i = 0; i < AW; ++i) o |= a[i];
+  for (int i = 0; i < AW; ++i) o |= a[i] | b[i];
   return o != 0u;
 }
 
-__device__ __forceinline__ uint32_t valid_bits(uint32_t N, uint32_t w) {
-  const uint32_t lo = w * 32u;
-  if (lo >= N) return 0u;
-  const uint32_t rem = N - lo;
-  return rem >= 32u ? FULL : ((1u << rem) - 1u);
-}
-
-// One step of the group test for literal l.
+// Stage A on 8 literals: gathers first, then the recurrence in order.
 template <int MODE, int AW>
-__device__ __forceinline__ void group_step(const PlaneView& pv, uint32_t l, uint32_t (&af)[AW], uint32_t (&ou)[AW]) {
-  uint32_t cf[AW];
-  load_agg<AW>(pv.aggF, l, cf);
-  if constexpr (MODE == GSS_MODE_ALLF) {
+__device__ __forceinline__ void group_batch8(const PlaneView& pv, const uint32_t (&l)[8], uint32_t (&af)[AW],
+                                             uint32_t (&ou)[AW]) {
+  constexpr int B = (AW == 4) ? 4 : 8;  // literals per sub-batch (bounds registers for wide rows)
 #pragma unroll
-    for (int i = 0; i < AW; ++i) af[i] &= cf[i];
-  } else {
-    uint32_t cu[AW];
-    load_agg<AW>(pv.aggU, l >> 1, cu);
+  for (int j0 = 0; j0 < 8; j0 += B) {
+    uint32_t cf[B][AW];
 #pragma unroll
-    for (int i = 0; i < AW; ++i) {
-      ou[i] = (af[i] & cu[i]) | (ou[i] & cf[i]);
-      af[i] &= cf[i];
+    for (int j = 0; j < B; ++j) load_agg<AW>(pv.aggF, l[j0 + j], cf[j]);
+    if constexpr (MODE == GSS_MODE_ALLF) {
+#pragma unroll
+      for (int j = 0; j < B; ++j)
+#pragma unroll
+        for (int i = 0; i < AW; ++i) af[i] &= cf[j][i];
+    } else {
+      uint32_t cu[B][AW];
+#pragma unroll
+      for (int j = 0; j < B; ++j) load_agg<AW>(pv.aggU, l[j0 + j] >> 1, cu[j]);
+#pragma unroll
+      for (int j = 0; j < B; ++j)
+#pragma unroll
+        for (int i = 0; i < AW; ++i) {
+          ou[i] = (af[i] & cu[j][i]) | (ou[i] & cf[j][i]);
+          af[i] &= cf[j][i];
+        }
     }
   }
 }
 
-// Exact recurrence for one literal on plane word g.
+// Stage B on 8 literals of one (clause, word g) pair.
 template <int MODE>
-__device__ __forceinline__ void word_step(const PlaneView& pv, uint32_t l, uint32_t g, uint32_t valid, uint32_t& af,
-                                          uint32_t& ou) {
-  const uint32_t F = __ldg(pv.P + (uint64_t)l * pv.Wp + g);
+__device__ __forceinline__ void word_batch8(const PlaneView& pv, const uint32_t (&l)[8], uint32_t g, uint32_t valid,
+                                            uint32_t& af, uint32_t& ou) {
+  uint32_t F[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) F[j] = __ldg(pv.P + (uint64_t)l[j] * pv.Wp + g);
   if constexpr (MODE == GSS_MODE_ALLF) {
-    af &= F;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) af &= F[j];
   } else {
-    const uint32_t T = __ldg(pv.P + (uint64_t)(l ^ 1u) * pv.Wp + g);
-    const uint32_t U = ~(F | T) & valid;
-    ou = (af & U) | (ou & F);
-    af &= F;
+    uint32_t T[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) T[j] = __ldg(pv.P + (uint64_t)(l[j] ^ 1u) * pv.Wp + g);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const uint32_t U = ~(F[j] | T[j]) & valid;
+      ou = (af & U) | (ou & F[j]);
+      af &= F[j];
+    }
   }
 }
 
-template <int MODE>
-__device__ __forceinline__ uint32_t exact_word(const ClauseView& db, const PlaneView& pv, uint64_t c,
-                                               const uint32_t (&l)[HEAD_K], bool has_tail, uint32_t g) {
-  const uint32_t valid = valid_bits(pv.N, g);
-  uint32_t af = valid, ou = 0u;
+__device__ __forceinline__ void load8_global(const uint32_t* p, uint32_t (&l)[8]) {
+  const uint4 a = __ldg(reinterpret_cast<const uint4*>(p)), b = __ldg(reinterpret_cast<const uint4*>(p) + 1);
+  l[0] = a.x; l[1] = a.y; l[2] = a.z; l[3] = a.w;
+  l[4] = b.x; l[5] = b.y; l[6] = b.z; l[7] = b.w;
+}
+
+// Literals [b, e) of the CSR as 8-literal chunks, PAD past e.
+__device__ __forceinline__ void load8_csr(const uint32_t* __restrict__ lits, uint64_t k0, uint64_t e, uint32_t pad,
+                                          uint32_t (&l)[8]) {
 #pragma unroll
-  for (uint32_t k = 0; k < HEAD_K; ++k)
-    if (l[k] != db.pad && (af | ou) != 0u) word_step<MODE>(pv, l[k], g, valid, af, ou);
-  if (has_tail && (af | ou) != 0u) {
-    const uint64_t b = db.off[c] + HEAD_K, e = db.off[c + 1];
-    for (uint64_t k = b; k < e && (af | ou) != 0u; ++k) word_step<MODE>(pv, __ldg(db.lits + k), g, valid, af, ou);
+  for (int j = 0; j < 8; ++j) l[j] = (k0 + j < e) ? __ldg(lits + k0 + j) : pad;
+}
+
+// Exact recurrence of one (clause, word) pair over all the clause's literals.
+template <int MODE>
+__device__ __forceinline__ uint32_t exact_pair(const ClauseView& db, const PlaneView& pv, uint64_t c,
+                                               const uint32_t* __restrict__ h0 /* shared */, uint32_t g) {
+  const uint32_t valid = valid_bits(pv.N, g);
+  uint32_t af = (MODE == GSS_MODE_ALLF) ? FULL : valid, ou = 0u;
+  uint32_t l[8];
+  const uint4 a = reinterpret_cast<const uint4*>(h0)[0], b = reinterpret_cast<const uint4*>(h0)[1];
+  l[0] = a.x; l[1] = a.y; l[2] = a.z; l[3] = a.w;
+  l[4] = b.x; l[5] = b.y; l[6] = b.z; l[7] = b.w;
+  word_batch8<MODE>(pv, l, g, valid, af, ou);
+  if ((af | ou) != 0u && l[7] != db.pad) {
+    load8_global(db.head1 + c * 8u, l);
+    word_batch8<MODE>(pv, l, g, valid, af, ou);
+    if ((af | ou) != 0u && l[7] != db.pad) {
+      const uint64_t e = db.off[c + 1];
+      for (uint64_t k0 = db.off[c] + HEAD_K; k0 < e && (af | ou) != 0u; k0 += 8) {
+        load8_csr(db.lits, k0, e, db.pad, l);
+        word_batch8<MODE>(pv, l, g, valid, af, ou);
+      }
+    }
   }
   return af | ou;
 }
 
 __device__ __forceinline__ void warp_append(bool has, uint32_t c, uint32_t g, uint32_t mask, uint32_t lane,
-                                            gss_report* __restrict__ rec, uint64_t cap,
-                                            unsigned long long* cnt) {
+                                            gss_report* __restrict__ rec, uint64_t cap, unsigned long long* cnt) {
   const uint32_t ball = __ballot_sync(FULL, has);
   if (ball == 0u) return;
   const int leader = __ffs(ball) - 1;
@@ -130,79 +231,116 @@ __device__ __forceinline__ void warp_append(bool has, uint32_t c, uint32_t g, ui
 template <int MODE, int AW>
 __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c_lo, uint64_t c_hi, PlaneView pv,
                                                        gss_report* __restrict__ rec, uint64_t cap, DevStatus* st) {
+  __shared__ WarpSmem smem[TEST_WARPS];
   if (st->bad_code) return;  // the assignment set held an invalid value code: no records
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint64_t warp_id = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-  const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+  WarpSmem& S = smem[wib];
+  const uint64_t warp_id = (uint64_t)blockIdx.x * TEST_WARPS + wib;
+  const uint64_t n_warps = (uint64_t)gridDim.x * TEST_WARPS;
+  const uint64_t n_tiles = (c_hi - c_lo + 31) / 32;
   const uint32_t PAD = db.pad;
+  if (warp_id >= n_tiles) return;
 
-  for (uint64_t tile = c_lo + warp_id * 32u; tile < c_hi; tile += n_warps * 32u) {
-    const uint64_t c = tile + lane;
-    const bool act = c < c_hi;
-    uint32_t l[HEAD_K];
-    if (act) {
-      const uint4* hp = reinterpret_cast<const uint4*>(db.head + c * HEAD_K);
-      const uint4 h0 = __ldcs(hp), h1 = __ldcs(hp + 1);
-      l[0] = h0.x; l[1] = h0.y; l[2] = h0.z; l[3] = h0.w;
-      l[4] = h1.x; l[5] = h1.y; l[6] = h1.z; l[7] = h1.w;
-    } else {
-#pragma unroll
-      for (uint32_t k = 0; k < HEAD_K; ++k) l[k] = PAD;
+  if (lane == 0) {
+    mbar_init(&S.bar[0], 1);
+    mbar_init(&S.bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  auto issue = [&](uint64_t tile, int stage) {  // lane 0: bulk-copy the tile's head0 into ring[stage]
+    const uint64_t c0 = c_lo + tile * 32u;
+    const uint64_t left = c_hi - c0;
+    const uint32_t n = left < 32u ? (uint32_t)left : 32u;
+    fence_proxy_async();
+    mbar_expect_tx(&S.bar[stage], n * 32u);
+    bulk_g2s(S.ring[stage], db.head0 + c0 * 8u, n * 32u, &S.bar[stage]);
+  };
+  if (lane == 0) issue(warp_id, 0);
+
+  uint32_t it = 0;
+  for (uint64_t t = warp_id; t < n_tiles; t += n_warps, ++it) {
+    const int s = it & 1;
+    const bool has_next = t + n_warps < n_tiles;
+    if (lane == 0 && has_next) issue(t + n_warps, s ^ 1);
+    const bool ok = mbar_wait(&S.bar[s], (it >> 1) & 1u);
+    if (!__all_sync(FULL, ok)) {  // bounded wait gave up: flag it, drain our copies (bounded), leave
+      if (lane == 0) {
+        atomicOr(&st->timeout, 1u);
+        mbar_wait(&S.bar[s], (it >> 1) & 1u);
+        if (has_next) mbar_wait(&S.bar[s ^ 1], ((it + 1) >> 1) & 1u);
+      }
+      __syncwarp();
+      return;
     }
-    const bool has_tail = act && l[HEAD_K - 1] != PAD;
+    const uint64_t c0 = c_lo + t * 32u;
+    const uint64_t c = c0 + lane;
+    const bool act = c < c_hi;
+    const uint32_t* h0 = &S.ring[s][lane * 8u];
 
-    // ---- stage A: group (aggregate) test
+    // ---------------- stage A: group (aggregate) test of this lane's clause
     uint32_t af[AW], ou[AW];
 #pragma unroll
     for (int i = 0; i < AW; ++i) { af[i] = act ? FULL : 0u; ou[i] = 0u; }
-    if constexpr (MODE == GSS_MODE_ALLF) {
-      // PAD rows are all ones, so the head is ANDed branch-free in two batches of four
-      // (four gathers in flight, then a second round only if some group is still alive).
-#pragma unroll
-      for (uint32_t k = 0; k < 4; ++k) group_step<MODE, AW>(pv, l[k], af, ou);
-      if (any_bit<AW>(af)) {
-#pragma unroll
-        for (uint32_t k = 4; k < HEAD_K; ++k) group_step<MODE, AW>(pv, l[k], af, ou);
-      }
-    } else {
-#pragma unroll
-      for (uint32_t k = 0; k < HEAD_K; ++k) {
-        uint32_t alive[AW];
-#pragma unroll
-        for (int i = 0; i < AW; ++i) alive[i] = af[i] | ou[i];
-        if (l[k] != PAD && any_bit<AW>(alive)) group_step<MODE, AW>(pv, l[k], af, ou);
+    if (act) {
+      uint32_t l[8];
+      const uint4 a = reinterpret_cast<const uint4*>(h0)[0], b = reinterpret_cast<const uint4*>(h0)[1];
+      l[0] = a.x; l[1] = a.y; l[2] = a.z; l[3] = a.w;
+      l[4] = b.x; l[5] = b.y; l[6] = b.z; l[7] = b.w;
+      group_batch8<MODE, AW>(pv, l, af, ou);
+      if (l[7] != PAD && any2<AW>(af, ou)) {
+        load8_global(db.head1 + c * 8u, l);
+        group_batch8<MODE, AW>(pv, l, af, ou);
+        if (l[7] != PAD && any2<AW>(af, ou)) {
+          const uint64_t e = db.off[c + 1];
+          for (uint64_t k0 = db.off[c] + HEAD_K; k0 < e && any2<AW>(af, ou); k0 += 8) {
+            load8_csr(db.lits, k0, e, PAD, l);
+            group_batch8<MODE, AW>(pv, l, af, ou);
+          }
+        }
       }
     }
     uint32_t cand[AW];
 #pragma unroll
     for (int i = 0; i < AW; ++i) cand[i] = af[i] | ou[i];
-    if (has_tail && any_bit<AW>(cand)) {
-      const uint64_t b = db.off[c] + HEAD_K, e = db.off[c + 1];
-      for (uint64_t k = b; k < e; ++k) {
-        group_step<MODE, AW>(pv, __ldg(db.lits + k), af, ou);
-#pragma unroll
-        for (int i = 0; i < AW; ++i) cand[i] = af[i] | ou[i];
-        if (!any_bit<AW>(cand)) break;
-      }
-    }
 
-    // ---- stage B: exact test of each surviving group, warp-aggregated append
-    while (__any_sync(FULL, any_bit<AW>(cand))) {
-      uint32_t g = 0u, res = 0u;
-      if (any_bit<AW>(cand)) {
-        bool found = false;
+    // ---------------- stage B: exact test of the warp's candidate (clause, group) pairs
+    for (;;) {
+      uint32_t cnt = 0;
 #pragma unroll
-        for (int i = 0; i < AW; ++i) {
-          if (!found && cand[i] != 0u) {
-            g = 32u * i + (uint32_t)(__ffs(cand[i]) - 1);
-            cand[i] &= cand[i] - 1u;
-            found = true;
-          }
-        }
-        res = exact_word<MODE>(db, pv, c, l, has_tail, g);
+      for (int i = 0; i < AW; ++i) cnt += __popc(cand[i]);
+      const uint32_t total = __reduce_add_sync(FULL, cnt);
+      if (total == 0u) break;
+      uint32_t incl = cnt;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, incl, d);
+        if (lane >= (uint32_t)d) incl += y;
       }
-      warp_append(res != 0u, (uint32_t)c, g, res, lane, rec, cap, &st->n_records);
+      uint32_t pos = incl - cnt;
+#pragma unroll
+      for (int i = 0; i < AW; ++i) {
+        while (cand[i] != 0u && pos < PAIR_CAP) {
+          const uint32_t bit = (uint32_t)(__ffs(cand[i]) - 1);
+          cand[i] &= cand[i] - 1u;
+          S.pairs[pos++] = lane | ((32u * i + bit) << 5);
+        }
+      }
+      __syncwarp();
+      const uint32_t np = total < PAIR_CAP ? total : PAIR_CAP;
+      for (uint32_t p0 = 0; p0 < np; p0 += 32u) {
+        const uint32_t p = p0 + lane;
+        uint32_t res = 0u, g = 0u, owner = 0u;
+        if (p < np) {
+          const uint32_t e = S.pairs[p];
+          owner = e & 31u;
+          g = e >> 5;
+          res = exact_pair<MODE>(db, pv, c0 + owner, &S.ring[s][owner * 8u], g);
+        }
+        warp_append(res != 0u, (uint32_t)(c0 + owner), g, res, lane, rec, cap, &st->n_records);
+      }
+      __syncwarp();
     }
+    __syncwarp();
   }
 }
 
@@ -227,7 +365,7 @@ cudaError_t launch_test(int mode, const ClauseView& db, uint64_t c_lo, uint64_t 
                         gss_report* rec, uint64_t cap, DevStatus* st, int grid, cudaStream_t s) {
   if (c_hi <= c_lo) return cudaSuccess;
   const uint64_t tiles = (c_hi - c_lo + 31) / 32;
-  const uint64_t max_blocks = (tiles + (TEST_THREADS / 32) - 1) / (TEST_THREADS / 32);
+  const uint64_t max_blocks = (tiles + TEST_WARPS - 1) / TEST_WARPS;
   if ((uint64_t)grid > max_blocks) grid = (int)max_blocks;
   if (grid < 1) grid = 1;
   if (mode == GSS_MODE_ALLF) {

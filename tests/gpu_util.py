@@ -7,7 +7,7 @@ import paper_2012_03119_gb300 as gss
 def gpu_records(inst, mode=gss.GSS_MODE_ALLF, report_capacity=None, max_assignments=None, codes=None):
     codes = inst.codes if codes is None else codes
     N = codes.shape[0]
-    cap = report_capacity or max(1024, 4 * inst.n_clauses)
+    cap = report_capacity or max(1024, inst.n_clauses * max(1, (N + 31) // 32))  # one record per (clause, word) at most
     with gss.Context(inst.n_vars, report_capacity=cap, max_assignments=max_assignments or max(N, 1),
                      mode=mode) as ctx:
         ctx.add_clauses(inst.offsets, inst.lits)
