@@ -146,7 +146,7 @@ int gss_set_assignments(gss_ctx* ctx, const uint8_t* values, uint32_t n_assign);
  * As gss_set_assignments, but `d_values` is a DEVICE pointer on the
  * context's device, rows `pitch` bytes apart (pitch >= n_vars), the buffer
  * spanning n_assign * pitch bytes.  Bytes past n_vars in a row are ignored.
- * When pitch and the pointer are multiples of 4 the codes are packed in
+ * When pitch and the pointer are multiples of 16 the codes are packed in
  * place; otherwise they are first copied (device to device) into a context
  * buffer.  The buffer must stay valid until the queued work has run.
  */

@@ -326,7 +326,8 @@ static int set_assignments_common(gss_ctx* c, const uint8_t* src, uint64_t pitch
   const uint32_t AWp = agg_stride(Wp);
   const uint8_t* codes = src;
   uint64_t cpitch = pitch;
-  const bool aligned = device_src && pitch % 4 == 0 && (reinterpret_cast<uintptr_t>(src) % 4) == 0;
+  // the packing kernel reads codes with 2-D TMA boxes: rows 16-byte aligned
+  const bool aligned = device_src && pitch % 16 == 0 && (reinterpret_cast<uintptr_t>(src) % 16) == 0;
   if (n && !aligned) {  // host data, or a device layout the packing kernel cannot read as 32-bit words
     if (c->codes_rows < n) {
       dev_free(c, c->codes);

@@ -52,8 +52,8 @@ struct ClauseView {
 };
 
 // ---------------------------------------------------------------- launchers
-// Pack value codes [N][pitch] (device) into P, aggF, aggU.  pitch % 4 == 0 and the
-// base 4-byte aligned.  Rows for PAD are written too.
+// Pack value codes [N][pitch] (device) into P, aggF, aggU.  pitch % 16 == 0 and the
+// base 16-byte aligned (TMA).  Rows for PAD are written too.
 cudaError_t launch_pack(const uint8_t* codes, uint64_t pitch, uint32_t V, uint32_t N, uint32_t Wp, uint32_t AWp,
                         uint32_t* P, uint32_t* aggF, uint32_t* aggU, DevStatus* st, cudaStream_t s);
 

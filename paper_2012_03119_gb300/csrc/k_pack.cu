@@ -12,22 +12,45 @@
 //   aggF[l] bit g = (P[l][g] != 0)      -- F is in G(l)
 //   aggU[v] bit g = some assignment of group g leaves v U   -- U is in G(v)
 //
-// Input: value codes [N][pitch] bytes (0 = U, 1 = T, 2 = F).  One CTA owns 128
-// variables and every assignment word.  Each lane reads 4 codes (one 32-bit word)
-// of a row, so a warp reads one 128-byte line per assignment row.  Bits are
-// gathered with shifts into four 8-row accumulators and transposed with byte
-// permutes; results are staged in shared memory in a layout that is bank-conflict
-// free on both the write (by lane) and the coalesced read-out (by plane word).
+// Structure: two persistent CTAs per SM.  A producer warp streams the value codes
+// [N][pitch] as 2-D TMA boxes of 32 assignment rows x 128 variables (4 KiB: one
+// plane word of 128 variables) into shared memory; rows past N and variables past V
+// arrive as zeros (U).  Word w of a variable tile belongs to consumer warp w % 8,
+// which owns PK_DEPTH stages of the ring and uses them in its own program order, so
+// each full / empty mbarrier is waited on at most one phase ahead (a parity wait
+// cannot be fooled by a stage two uses behind).  Eight
+// consumer warps transpose boxes: a lane takes 4 codes of each of the 32 rows; the
+// F bit (bit 1 of a code byte) and the T bit (bit 0) move to bit r % 8 of their byte
+// with one shift and one fused and-or each, and byte permutes turn four 8-row
+// accumulators into per-variable words.  Words are staged in shared memory at an odd
+// stride, so the by-lane write and the coalesced by-word read-out are both
+// bank-conflict free; the read-out derives aggF / aggU with warp ballots.  The
+// producer keeps loading the next variables while consumers write out.
+#include <cudaTypedefs.h>
+
 #include "gss_internal.h"
+#include "gss_ptx.h"
 
 namespace gss {
 namespace {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
-constexpr int PK_VT = 128;                // variables per CTA (4 per lane)
-constexpr int PK_THREADS = 256;           // 8 warps
-constexpr int PK_WARPS = PK_THREADS / 32;
-constexpr int PK_STRIDE = 2 * PK_VT + 1;  // staged words per plane word (odd => conflict-free read-out)
+constexpr int PK_VT = 128;                         // variables per box (bytes per box row)
+constexpr int PK_ROWS = 32;                        // assignment rows per box: one plane word
+constexpr int PK_CONSUMERS = 8;                    // consumer warps
+constexpr int PK_DEPTH = 2;                        // stages owned by each consumer warp
+constexpr int PK_STAGES = PK_CONSUMERS * PK_DEPTH; // ring depth
+constexpr int PK_THREADS = 32 * (PK_CONSUMERS + 1);
+constexpr int PK_BOX = PK_VT * PK_ROWS;            // 8 KiB
+constexpr int PK_STRIDE = 2 * PK_VT + 1;           // staged words per plane word (odd)
+constexpr uint32_t BAR_CONSUMERS = 1;              // named barrier of the consumer warps
+
+struct PackSmem {
+  uint8_t ring[PK_STAGES][PK_BOX];
+  uint32_t stage[32 * PK_STRIDE];
+  unsigned long long full[PK_STAGES], empty[PK_STAGES];
+  volatile int err;
+};
 
 __device__ __forceinline__ uint32_t valid_bits(uint32_t N, uint32_t w) {
   const uint32_t lo = w * 32u;
@@ -36,81 +59,163 @@ __device__ __forceinline__ uint32_t valid_bits(uint32_t N, uint32_t w) {
   return rem >= 32u ? FULL : ((1u << rem) - 1u);
 }
 
-__global__ void __launch_bounds__(PK_THREADS) k_pack(const uint8_t* __restrict__ codes, uint64_t pitch, uint32_t V,
-                                                     uint32_t N, uint32_t Wp, uint32_t AWp, uint32_t* __restrict__ P,
-                                                     uint32_t* __restrict__ aggF, uint32_t* __restrict__ aggU,
-                                                     DevStatus* st) {
-  __shared__ uint32_t stage[32 * PK_STRIDE];
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  const uint32_t v0 = blockIdx.x * PK_VT;
-  const uint32_t vlane = v0 + 4u * lane;  // first of this lane's 4 variables
-  uint32_t bmask = 0;                     // bytes of the lane's word that are real variables
-  if (vlane < V) bmask = (V - vlane >= 4u) ? FULL : ((1u << (8u * (V - vlane))) - 1u);
-  const uint32_t nv = min((uint32_t)PK_VT, V - v0);
-  uint32_t bad = 0;
+// Sequence number, among the boxes of consumer warp q = w % 8 in this CTA, of word w of
+// variable tile t (the CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...).
+__device__ __forceinline__ uint32_t word_seq(uint32_t q, uint32_t t, uint32_t w, uint32_t Wd, uint32_t b,
+                                             uint32_t g) {
+  const uint32_t per_tile = Wd > q ? (Wd - q + PK_CONSUMERS - 1) / PK_CONSUMERS : 0u;  // words of warp q per tile
+  const uint32_t i = (t - b) / g;                                                      // tiles done before t
+  return i * per_tile + w / PK_CONSUMERS;
+}
+__device__ __forceinline__ uint32_t stage_of(uint32_t q, uint32_t t, uint32_t w, uint32_t Wd, uint32_t b,
+                                             uint32_t g) {
+  return q + PK_CONSUMERS * (word_seq(q, t, w, Wd, b, g) % PK_DEPTH);
+}
 
-  for (uint32_t wc = 0; wc < Wp; wc += 32u) {
-    const uint32_t nw = min(32u, Wp - wc);  // 4, 8, 16 or 32
-    // Phase 1: warp `warp` builds plane words wc + wl for its 128 variables.
-    for (uint32_t wl = warp; wl < nw; wl += PK_WARPS) {
-      const uint32_t w = wc + wl;
-      uint32_t f[4] = {0u, 0u, 0u, 0u}, t[4] = {0u, 0u, 0u, 0u};
-      if (bmask != 0u && w * 32u < N) {
-        const uint8_t* base = codes + (uint64_t)w * 32u * pitch + vlane;
+__global__ void __launch_bounds__(PK_THREADS, 2) k_pack(const __grid_constant__ CUtensorMap map, uint32_t V,
+                                                        uint32_t N, uint32_t Wp, uint32_t AWp,
+                                                        uint32_t* __restrict__ P, uint32_t* __restrict__ aggF,
+                                                        uint32_t* __restrict__ aggU, DevStatus* st) {
+  extern __shared__ uint8_t smem_raw[];
+  PackSmem& S = *reinterpret_cast<PackSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  const uint32_t n_vt = (V + PK_VT - 1) / PK_VT;
+  const uint32_t Wd = (N + 31) / 32;  // plane words that hold assignments
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < PK_STAGES; ++s) {
+      ptx::mbar_init(&S.full[s], 1);
+      ptx::mbar_init(&S.empty[s], 1);
+    }
+    S.err = 0;
+    ptx::fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (warp == PK_CONSUMERS) {  // ---------------- producer
+    if (lane == 0) {
+      ptx::prefetch_tensormap(&map);
+      uint32_t uses[PK_STAGES];  // loads issued into each stage so far
+      for (int s = 0; s < PK_STAGES; ++s) uses[s] = 0u;
+      bool ok = true;
+      for (uint32_t t = blockIdx.x; t < n_vt && ok; t += gridDim.x) {
+        for (uint32_t w = 0; w < Wd; ++w) {
+          // word w goes to consumer q = w % 8; its m-th word of this CTA uses stage q + 8 (m % DEPTH)
+          const uint32_t q = w % PK_CONSUMERS;
+          const uint32_t s = stage_of(q, t, w, Wd, blockIdx.x, gridDim.x);
+          if (uses[s] > 0u) ok = ptx::mbar_wait(&S.empty[s], (uses[s] - 1u) & 1u);  // previous use consumed
+          if (!ok || S.err) { ok = false; break; }
+          ptx::mbar_expect_tx(&S.full[s], PK_BOX);
+          ptx::tma_load_2d(S.ring[s], &map, (int32_t)(t * PK_VT), (int32_t)(w * PK_ROWS), &S.full[s]);
+          ++uses[s];
+        }
+      }
+      if (!ok) {
+        S.err = 1;
+        atomicOr(&st->timeout, 1u);
+      }
+      // every issued box must have landed before the CTA may exit (bounded)
+      for (int s = 0; s < PK_STAGES; ++s)
+        if (uses[s] > 0u) ptx::mbar_wait(&S.full[s], (uses[s] - 1u) & 1u);
+    }
+    return;
+  }
+
+  // ---------------- consumers
+  uint32_t bad = 0;
+  for (uint32_t t = blockIdx.x; t < n_vt; t += gridDim.x) {
+    const uint32_t v0 = t * PK_VT;
+    const uint32_t nv = min((uint32_t)PK_VT, V - v0);
+    for (uint32_t wc = 0; wc < Wp; wc += 32u) {
+      const uint32_t nw = min(32u, Wp - wc);  // 4, 8, 16 or 32 words in this pass (one aggregate word)
+      const uint32_t lg_nw = 31u - __clz(nw);
+      for (uint32_t wl = warp; wl < nw; wl += PK_CONSUMERS) {
+        const uint32_t w = wc + wl;
+        uint32_t f[4] = {0u, 0u, 0u, 0u}, tt[4] = {0u, 0u, 0u, 0u};
+        if (w < Wd) {
+          const uint32_t m = word_seq(warp, t, w, Wd, blockIdx.x, gridDim.x);
+          const uint32_t s = warp + PK_CONSUMERS * (m % PK_DEPTH);
+          bool ok = !S.err && ptx::mbar_wait(&S.full[s], (m / PK_DEPTH) & 1u);
+          if (!__all_sync(FULL, ok)) {
+            if (lane == 0 && !S.err) {
+              S.err = 1;
+              atomicOr(&st->timeout, 1u);
+            }
+          } else {
+            const uint8_t* box = S.ring[s] + 4u * lane;
+            uint32_t any = 0u;
 #pragma unroll
-        for (int r = 0; r < 32; ++r) {
-          uint32_t x = 0u;
-          if (w * 32u + (uint32_t)r < N)
-            x = __ldcs(reinterpret_cast<const unsigned int*>(base + (uint64_t)r * pitch)) & bmask;
-          bad |= (x & 0xFCFCFCFCu) | (x & (x >> 1) & 0x01010101u);  // code 3 or above
-          f[r >> 3] |= ((x >> 1) & 0x01010101u) << (r & 7);         // code 2 = F
-          t[r >> 3] |= (x & 0x01010101u) << (r & 7);                // code 1 = T
+            for (int r = 0; r < 32; ++r) {
+              const uint32_t x = *reinterpret_cast<const uint32_t*>(box + r * PK_VT);
+              const int sh = r & 7;
+              any |= x;
+              if (sh == 0) f[r >> 3] |= (x >> 1) & 0x01010101u;
+              else f[r >> 3] |= (x << (sh - 1)) & (0x01010101u << sh);
+              tt[r >> 3] |= (x << sh) & (0x01010101u << sh);
+            }
+            // invalid codes: a bit above bit 1 of a byte, or code 3 (F and T bits both set)
+            bad |= (any & 0xFCFCFCFCu) | (f[0] & tt[0]) | (f[1] & tt[1]) | (f[2] & tt[2]) | (f[3] & tt[3]);
+          }
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&S.empty[s]);  // the box may be overwritten now
+        }
+        // byte k of f[j] holds rows 8j..8j+7 of variable v0 + 4 lane + k
+        const uint32_t fa = __byte_perm(f[0], f[1], 0x5140), fb = __byte_perm(f[2], f[3], 0x5140);
+        const uint32_t fc = __byte_perm(f[0], f[1], 0x7362), fd = __byte_perm(f[2], f[3], 0x7362);
+        const uint32_t ta = __byte_perm(tt[0], tt[1], 0x5140), tb = __byte_perm(tt[2], tt[3], 0x5140);
+        const uint32_t tc = __byte_perm(tt[0], tt[1], 0x7362), td = __byte_perm(tt[2], tt[3], 0x7362);
+        // staged index of (variable 4 lane + k, literal sign s) = (2 k + s) * 32 + lane
+        uint32_t* sw = S.stage + wl * PK_STRIDE + lane;
+        sw[0 * 32] = __byte_perm(fa, fb, 0x5410);
+        sw[1 * 32] = __byte_perm(ta, tb, 0x5410);
+        sw[2 * 32] = __byte_perm(fa, fb, 0x7632);
+        sw[3 * 32] = __byte_perm(ta, tb, 0x7632);
+        sw[4 * 32] = __byte_perm(fc, fd, 0x5410);
+        sw[5 * 32] = __byte_perm(tc, td, 0x5410);
+        sw[6 * 32] = __byte_perm(fc, fd, 0x7632);
+        sw[7 * 32] = __byte_perm(tc, td, 0x7632);
+      }
+      ptx::named_bar_sync(BAR_CONSUMERS, 32 * PK_CONSUMERS);
+      // coalesced write-out over (variable, word) pairs, word index fastest
+      const uint32_t total = PK_VT * nw;  // a multiple of 32: every lane runs the same trip count
+      for (uint32_t i = threadIdx.x; i < total; i += 32 * PK_CONSUMERS) {
+        const uint32_t vl = i >> lg_nw, wl = i & (nw - 1u);
+        const uint32_t kv = vl & 3u, ln = vl >> 2;
+        const uint32_t Fw = S.stage[wl * PK_STRIDE + (2u * kv) * 32u + ln];
+        const uint32_t Tw = S.stage[wl * PK_STRIDE + (2u * kv + 1u) * 32u + ln];
+        const uint32_t w = wc + wl;
+        const uint32_t Uw = ~(Fw | Tw) & valid_bits(N, w);
+        const uint32_t bF = __ballot_sync(FULL, Fw != 0u);
+        const uint32_t bT = __ballot_sync(FULL, Tw != 0u);
+        const uint32_t bU = __ballot_sync(FULL, Uw != 0u);
+        if (vl < nv) {
+          const uint64_t v = v0 + vl;
+          P[(2u * v) * Wp + w] = Fw;
+          P[(2u * v + 1u) * Wp + w] = Tw;
+          if (wl == 0u) {  // this variable's nw words sit in lanes [lane, lane + nw); one aggregate word per pass
+            const uint32_t m = nw == 32u ? FULL : ((1u << nw) - 1u);
+            const uint32_t u = wc >> 5;
+            aggF[(2u * v) * AWp + u] = (bF >> lane) & m;
+            aggF[(2u * v + 1u) * AWp + u] = (bT >> lane) & m;
+            aggU[v * AWp + u] = (bU >> lane) & m;
+          }
         }
       }
-      // byte k of f[j] holds rows 8j..8j+7 of variable vlane+k; gather the four bytes of each variable
-      const uint32_t fa = __byte_perm(f[0], f[1], 0x5140), fb = __byte_perm(f[2], f[3], 0x5140);
-      const uint32_t fc = __byte_perm(f[0], f[1], 0x7362), fd = __byte_perm(f[2], f[3], 0x7362);
-      const uint32_t ta = __byte_perm(t[0], t[1], 0x5140), tb = __byte_perm(t[2], t[3], 0x5140);
-      const uint32_t tc = __byte_perm(t[0], t[1], 0x7362), td = __byte_perm(t[2], t[3], 0x7362);
-      uint32_t* sw = stage + wl * PK_STRIDE + lane;
-      sw[0 * 32] = __byte_perm(fa, fb, 0x5410);  // variable vlane+0: F word
-      sw[1 * 32] = __byte_perm(ta, tb, 0x5410);  //                  T word
-      sw[2 * 32] = __byte_perm(fa, fb, 0x7632);  // variable vlane+1
-      sw[3 * 32] = __byte_perm(ta, tb, 0x7632);
-      sw[4 * 32] = __byte_perm(fc, fd, 0x5410);  // variable vlane+2
-      sw[5 * 32] = __byte_perm(tc, td, 0x5410);
-      sw[6 * 32] = __byte_perm(fc, fd, 0x7632);  // variable vlane+3
-      sw[7 * 32] = __byte_perm(tc, td, 0x7632);
+      ptx::named_bar_sync(BAR_CONSUMERS, 32 * PK_CONSUMERS);
     }
-    __syncthreads();
-    // Phase 2: coalesced write-out, (variable, word) pairs with the word index fastest.
-    const uint32_t total = PK_VT * nw;  // a multiple of 32: every lane runs the same trip count
-    for (uint32_t i = threadIdx.x; i < total; i += PK_THREADS) {
-      const uint32_t vl = i / nw, wl = i - vl * nw;
-      const uint32_t k = vl & 3u, ln = vl >> 2;
-      const uint32_t Fw = stage[wl * PK_STRIDE + (2u * k) * 32u + ln];
-      const uint32_t Tw = stage[wl * PK_STRIDE + (2u * k + 1u) * 32u + ln];
-      const uint32_t w = wc + wl;
-      const uint32_t Uw = ~(Fw | Tw) & valid_bits(N, w);
-      const uint32_t bF = __ballot_sync(FULL, Fw != 0u);
-      const uint32_t bT = __ballot_sync(FULL, Tw != 0u);
-      const uint32_t bU = __ballot_sync(FULL, Uw != 0u);
-      if (vl < nv) {
-        const uint64_t v = v0 + vl;
-        P[(2u * v) * Wp + w] = Fw;
-        P[(2u * v + 1u) * Wp + w] = Tw;
-        if (wl == 0u) {  // this variable's nw words sit in lanes [lane, lane + nw)
-          const uint32_t m = nw == 32u ? FULL : ((1u << nw) - 1u);
-          const uint32_t u = wc >> 5;
-          aggF[(2u * v) * AWp + u] = (bF >> lane) & m;
-          aggF[(2u * v + 1u) * AWp + u] = (bT >> lane) & m;
-          aggU[v * AWp + u] = (bU >> lane) & m;
-        }
-      }
-    }
-    __syncthreads();
   }
   if (bad) atomicOr(&st->bad_code, 1u);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
 }
 
 }  // namespace
@@ -121,9 +226,29 @@ cudaError_t launch_pack(const uint8_t* codes, uint64_t pitch, uint32_t V, uint32
   cudaError_t e = cudaMemsetAsync(P + 2ull * V * Wp, 0xFF, 2ull * Wp * sizeof(uint32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(aggF + 2ull * V * AWp, 0xFF, 2ull * AWp * sizeof(uint32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(aggU + (uint64_t)V * AWp, 0, AWp * sizeof(uint32_t), s);
-  if (e != cudaSuccess || V == 0) return e;
-  const uint32_t grid = (V + PK_VT - 1) / PK_VT;
-  k_pack<<<grid, PK_THREADS, 0, s>>>(codes, pitch, V, N, Wp, AWp, P, aggF, aggU, st);
+  if (e != cudaSuccess || V == 0 || N == 0) return e;
+  if (pitch % 16 != 0 || reinterpret_cast<uintptr_t>(codes) % 16 != 0) return cudaErrorInvalidValue;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap map;
+  const cuuint64_t dims[2] = {V, N};
+  const cuuint64_t strides[1] = {pitch};
+  const cuuint32_t box[2] = {PK_VT, PK_ROWS};
+  const cuuint32_t estr[2] = {1, 1};
+  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(codes), dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  const size_t smem = sizeof(PackSmem) + 128;
+  e = cudaFuncSetAttribute(k_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, n_sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint32_t n_vt = (V + PK_VT - 1) / PK_VT;
+  const uint32_t slots = 2u * (uint32_t)n_sms;  // two CTAs fit on an SM
+  const uint32_t grid = n_vt < slots ? n_vt : slots;
+  k_pack<<<grid, PK_THREADS, smem, s>>>(map, V, N, Wp, AWp, P, aggF, aggU, st);
   return cudaGetLastError();
 }
 

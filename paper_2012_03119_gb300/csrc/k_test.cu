@@ -30,6 +30,7 @@
 // The PAD literal 2V is neutral in both modes: its P and aggF rows are all ones and its
 // aggU row is zero, so padded head slots need no branch.
 #include "gss_internal.h"
+#include "gss_ptx.h"
 
 namespace gss {
 namespace {
@@ -38,57 +39,12 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int TEST_THREADS = 256;
 constexpr int TEST_WARPS = TEST_THREADS / 32;
 constexpr uint32_t PAIR_CAP = 64;        // candidate pairs staged per warp per round
-constexpr uint64_t WAIT_NS = 1000000000; // bounded mbarrier wait: 1 s
 
 struct __align__(128) WarpSmem {
   uint32_t ring[2][32 * 8];  // head0 of the current and the next tile
   uint32_t pairs[PAIR_CAP];  // owner lane | group << 5
   unsigned long long bar[2];
 };
-
-// ------------------------------------------------------------------ PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-// Bulk copy global -> shared; both addresses 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ uint64_t globaltimer_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// Wait for phase `parity` of the barrier; gives up after WAIT_NS and returns false.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = globaltimer_ns();
-  for (uint32_t i = 0; i < (1u << 28); ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 63u) == 63u && globaltimer_ns() - t0 > WAIT_NS) return false;
-  }
-  return false;
-}
 
 // ------------------------------------------------------------------ math helpers
 __device__ __forceinline__ uint32_t valid_bits(uint32_t N, uint32_t w) {
@@ -242,18 +198,18 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c
   if (warp_id >= n_tiles) return;
 
   if (lane == 0) {
-    mbar_init(&S.bar[0], 1);
-    mbar_init(&S.bar[1], 1);
-    fence_mbar_init();
+    ptx::mbar_init(&S.bar[0], 1);
+    ptx::mbar_init(&S.bar[1], 1);
+    ptx::fence_mbar_init();
   }
   __syncwarp();
   auto issue = [&](uint64_t tile, int stage) {  // lane 0: bulk-copy the tile's head0 into ring[stage]
     const uint64_t c0 = c_lo + tile * 32u;
     const uint64_t left = c_hi - c0;
     const uint32_t n = left < 32u ? (uint32_t)left : 32u;
-    fence_proxy_async();
-    mbar_expect_tx(&S.bar[stage], n * 32u);
-    bulk_g2s(S.ring[stage], db.head0 + c0 * 8u, n * 32u, &S.bar[stage]);
+    ptx::fence_proxy_async();
+    ptx::mbar_expect_tx(&S.bar[stage], n * 32u);
+    ptx::bulk_g2s(S.ring[stage], db.head0 + c0 * 8u, n * 32u, &S.bar[stage]);
   };
   if (lane == 0) issue(warp_id, 0);
 
@@ -262,12 +218,12 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c
     const int s = it & 1;
     const bool has_next = t + n_warps < n_tiles;
     if (lane == 0 && has_next) issue(t + n_warps, s ^ 1);
-    const bool ok = mbar_wait(&S.bar[s], (it >> 1) & 1u);
+    const bool ok = ptx::mbar_wait(&S.bar[s], (it >> 1) & 1u);
     if (!__all_sync(FULL, ok)) {  // bounded wait gave up: flag it, drain our copies (bounded), leave
       if (lane == 0) {
         atomicOr(&st->timeout, 1u);
-        mbar_wait(&S.bar[s], (it >> 1) & 1u);
-        if (has_next) mbar_wait(&S.bar[s ^ 1], ((it + 1) >> 1) & 1u);
+        ptx::mbar_wait(&S.bar[s], (it >> 1) & 1u);
+        if (has_next) ptx::mbar_wait(&S.bar[s ^ 1], ((it + 1) >> 1) & 1u);
       }
       __syncwarp();
       return;
