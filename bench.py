@@ -195,6 +195,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--ref-assignments", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--layout", default="frequency", choices=["frequency", "identity"],
+                    help="internal variable numbering of the clause database")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -222,7 +224,8 @@ def main():
     stream = torch.cuda.Stream()
     N, V, m = inst.n_assign, inst.n_vars, inst.n_clauses
     cap = max(1 << 22, 8 * len(inst.planted) + 4 * m)
-    ctx = gss.Context(V, device=local, stream=stream, report_capacity=cap, max_assignments=max(N, 32))
+    layout = gss.GSS_LAYOUT_FREQUENCY if args.layout == "frequency" else gss.GSS_LAYOUT_IDENTITY
+    ctx = gss.Context(V, device=local, stream=stream, report_capacity=cap, max_assignments=max(N, 32), layout=layout)
 
     # a-1: ingest the database (once; the database stays resident like the paper's GPU clause store)
     torch.cuda.synchronize()
@@ -324,7 +327,8 @@ def main():
         "config": {"workload": workload, "n_vars": V, "n_clauses": m, "n_lits": inst.n_lits, "n_assign": N,
                    "seed": inst.params.get("seed"), "l2": "inputs larger than L2 (1 GB codes + 0.26 GB planes "
                    "streamed per step)" if args.config == "single" and args.scale == 1.0 else "see sizes",
-                   "parallelism": f"weak x{world}: one clause database per GPU, shared assignment set"},
+                   "parallelism": f"weak x{world}: one clause database per GPU, shared assignment set",
+                   "layout": args.layout},
         "e2e": {"value": units * e2e_steps / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": N * V,
                 "d2h_bytes_per_step": 12 * n_records + 48},
         "roofline": {k: v for k, v in roof[dominant].items()},

@@ -53,6 +53,15 @@ enum {
 
 enum { GSS_MODE_ALLF = 0, GSS_MODE_TRIGGER = 1 };
 
+/*
+ * Internal variable numbering.  GSS_LAYOUT_FREQUENCY (default): the first
+ * gss_add_clauses batch fixes an internal numbering, most frequent variables
+ * first, so the hottest literals' assignment rows sit together in memory (the
+ * locality Section 7 proposes to exploit).  GSS_LAYOUT_IDENTITY keeps the
+ * caller's numbering.  Reports are per clause id and identical either way.
+ */
+enum { GSS_LAYOUT_IDENTITY = 0, GSS_LAYOUT_FREQUENCY = 1 };
+
 #define GSS_MAX_ASSIGNMENTS 4096u /* largest N per assignment set */
 #define GSS_HEAD_WIDTH 16u        /* literals per clause kept in the head planes */
 
@@ -66,6 +75,7 @@ typedef struct {
   uint32_t max_assignments;  /* upper bound on N, <= GSS_MAX_ASSIGNMENTS (default 1024) */
   uint32_t mode;             /* GSS_MODE_ALLF (default) or GSS_MODE_TRIGGER */
   uint64_t mem_budget_bytes; /* cap on device bytes the context may hold; 0 = no cap */
+  uint32_t layout;           /* GSS_LAYOUT_FREQUENCY (default) or GSS_LAYOUT_IDENTITY */
 } gss_config;
 
 /*

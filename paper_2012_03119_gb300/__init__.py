@@ -23,6 +23,7 @@ __all__ = ["Context", "GssError", "REPORT_DTYPE", "expand_reports", "load", "GSS
 GSS_OK, GSS_E_INVAL, GSS_E_NOMEM, GSS_E_CUDA, GSS_E_OVERFLOW, GSS_E_TIMEOUT, GSS_E_BUSY, GSS_E_STATE = \
     0, -1, -2, -3, -4, -5, -6, -7
 GSS_MODE_ALLF, GSS_MODE_TRIGGER = 0, 1
+GSS_LAYOUT_IDENTITY, GSS_LAYOUT_FREQUENCY = 0, 1
 GSS_MAX_ASSIGNMENTS = 4096
 GSS_HEAD_WIDTH = 16
 
@@ -32,7 +33,7 @@ REPORT_DTYPE = np.dtype([("clause_id", "<u4"), ("word", "<u4"), ("mask", "<u4")]
 class gss_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("report_capacity", ctypes.c_uint64),
                 ("max_assignments", ctypes.c_uint32), ("mode", ctypes.c_uint32),
-                ("mem_budget_bytes", ctypes.c_uint64)]
+                ("mem_budget_bytes", ctypes.c_uint64), ("layout", ctypes.c_uint32)]
 
 
 class gss_stats(ctypes.Structure):
@@ -213,7 +214,8 @@ class Context:
     """Owns one ``gss_ctx``: a resident clause database, one assignment set and a report buffer."""
 
     def __init__(self, n_vars: int, device: int = 0, stream=None, report_capacity: int = 1 << 22,
-                 max_assignments: int = 1024, mode: int = GSS_MODE_ALLF, mem_budget_bytes: int = 0):
+                 max_assignments: int = 1024, mode: int = GSS_MODE_ALLF, mem_budget_bytes: int = 0,
+                 layout: int = GSS_LAYOUT_FREQUENCY):
         cfg = gss_config_init()
         cfg.device = device
         cfg.stream = ctypes.c_void_p(_stream_handle(stream)) if stream is not None else None
@@ -221,6 +223,7 @@ class Context:
         cfg.max_assignments = max_assignments
         cfg.mode = mode
         cfg.mem_budget_bytes = mem_budget_bytes
+        cfg.layout = layout
         self.n_vars = n_vars
         self._stream = stream
         self.ptr = gss_create(n_vars, cfg)

@@ -23,7 +23,7 @@ struct gss_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  uint32_t V = 0, max_N = 0, mode = GSS_MODE_ALLF;
+  uint32_t V = 0, max_N = 0, mode = GSS_MODE_ALLF, layout = GSS_LAYOUT_FREQUENCY;
   uint64_t budget = 0, bytes = 0;
   int n_sms = 1;
   std::unordered_map<void*, uint64_t> allocs;
@@ -35,6 +35,7 @@ struct gss_ctx {
   uint32_t* head0 = nullptr;
   uint32_t* head1 = nullptr;
   uint64_t* boff = nullptr;
+  uint32_t* map = nullptr;  // internal variable ids (frequency layout), fixed by the first batch
 
   // assignment set
   uint32_t N = 0, Wp = 4, AWp = 1;
@@ -206,6 +207,7 @@ int gss_config_init(gss_config* cfg) {
   cfg->max_assignments = 1024;
   cfg->mode = GSS_MODE_ALLF;
   cfg->mem_budget_bytes = 0;
+  cfg->layout = GSS_LAYOUT_FREQUENCY;
   return GSS_OK;
 }
 
@@ -217,6 +219,7 @@ int gss_create(gss_ctx** out, uint32_t n_vars, const gss_config* cfg_in) {
   if (n_vars == 0 || n_vars >= (1u << 31)) return GSS_E_INVAL;
   if (cfg.max_assignments == 0 || cfg.max_assignments > GSS_MAX_ASSIGNMENTS) return GSS_E_INVAL;
   if (cfg.mode != GSS_MODE_ALLF && cfg.mode != GSS_MODE_TRIGGER) return GSS_E_INVAL;
+  if (cfg.layout != GSS_LAYOUT_IDENTITY && cfg.layout != GSS_LAYOUT_FREQUENCY) return GSS_E_INVAL;
   int n_dev = 0;
   if (cudaGetDeviceCount(&n_dev) != cudaSuccess || cfg.device < 0 || cfg.device >= n_dev) {
     cudaGetLastError();
@@ -229,6 +232,7 @@ int gss_create(gss_ctx** out, uint32_t n_vars, const gss_config* cfg_in) {
   c->V = n_vars;
   c->max_N = cfg.max_assignments;
   c->mode = cfg.mode;
+  c->layout = cfg.layout;
   c->budget = cfg.mem_budget_bytes;
   c->Vp = (n_vars + 15ull) / 16 * 16;
   int rc = GSS_OK;
@@ -299,11 +303,30 @@ int gss_add_clauses(gss_ctx* c, const uint64_t* offsets, uint64_t n, const uint3
   CK(c, cudaMemsetAsync(c->st + 1, 0, sizeof(DevStatus), c->stream));
   CK(c, cudaMemcpyAsync(c->boff, offsets, (n + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, c->stream));
   if (L) CK(c, cudaMemcpyAsync(c->lits + c->L, lits, L * sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream));
-  CK(c, launch_ingest(c->boff, n, L, c->L, c->off + c->m, c->head0 + c->m * 8, c->head1 + c->m * 8, c->lits, c->V,
-                      c->st + 1, c->stream));
+  uint32_t* blits = c->lits + c->L;  // this batch's literals (caller numbering until translated)
+  CK(c, launch_validate(c->boff, n, L, c->L, c->off + c->m, blits, c->V, c->st + 1, c->stream));
   if ((rc = sync_status(c))) return rc;
   if (c->h_st[1].bad_size) return fail(c, GSS_E_INVAL, "empty clause or offsets not increasing / past the batch");
   if (c->h_st[1].bad_lit) return fail(c, GSS_E_INVAL, "literal >= 2 * n_vars (%u)", 2 * c->V);
+  if (c->layout == GSS_LAYOUT_FREQUENCY && !c->map) {  // the first batch fixes the numbering
+    void* pm = nullptr;
+    void* ps = nullptr;
+    if ((rc = dev_alloc(c, &pm, (uint64_t)c->V * sizeof(uint32_t)))) return rc;
+    if ((rc = dev_alloc(c, &ps, rank_scratch_words(c->V) * sizeof(uint32_t)))) {
+      dev_free(c, pm);
+      return rc;
+    }
+    cudaError_t e = launch_rank_vars(blits, L, c->V, static_cast<uint32_t*>(ps), static_cast<uint32_t*>(pm), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(c, ps);
+    if (e != cudaSuccess) {
+      dev_free(c, pm);
+      return fail(c, GSS_E_CUDA, "variable ranking: %s", cudaGetErrorString(e));
+    }
+    c->map = static_cast<uint32_t*>(pm);
+  }
+  if (c->map) CK(c, launch_translate(blits, L, c->map, c->stream));
+  CK(c, launch_build_heads(c->boff, n, c->L, c->head0 + c->m * 8, c->head1 + c->m * 8, c->lits, c->V, c->stream));
   if (first_id) *first_id = (uint32_t)c->m;
   c->m += n;
   c->L += L;
@@ -344,7 +367,7 @@ static int set_assignments_common(gss_ctx* c, const uint8_t* src, uint64_t pitch
     codes = c->codes;
     cpitch = c->Vp;
   }
-  if (n) CK(c, launch_pack(codes, cpitch, c->V, n, Wp, AWp, c->P, c->aggF, c->aggU, c->st, c->stream));
+  if (n) CK(c, launch_pack(codes, cpitch, c->V, n, Wp, AWp, c->map, c->P, c->aggF, c->aggU, c->st, c->stream));
   c->N = n;
   c->Wp = Wp;
   c->AWp = AWp;

@@ -5,6 +5,8 @@
 //   lits   u32 [L]               literals, l = 2v + s
 //   head0  u32 [m][8]            literals 0..7 of each clause, padded with PAD = 2V
 //   head1  u32 [m][8]            literals 8..15 of each clause, padded with PAD
+//   map    u32 [V]               internal id of each variable (hottest first); stored literals
+//                                and plane rows use internal ids
 //   P      u32 [2V + 2][Wp]      false planes: P[l][w] bit j set iff assignment 32w + j gives
 //                                literal l the value F (P[2v] = isFalse(v), P[2v+1] = isTrue(v));
 //                                rows 2V, 2V + 1 are all ones (PAD is neutral under AND)
@@ -52,16 +54,23 @@ struct ClauseView {
 };
 
 // ---------------------------------------------------------------- launchers
-// Pack value codes [N][pitch] (device) into P, aggF, aggU.  pitch % 16 == 0 and the
-// base 16-byte aligned (TMA).  Rows for PAD are written too.
+// Pack value codes [N][pitch] (device) into P, aggF, aggU, variable v at row map[v] (identity
+// when map is null).  pitch % 16 == 0 and the base 16-byte aligned (TMA).  PAD rows too.
 cudaError_t launch_pack(const uint8_t* codes, uint64_t pitch, uint32_t V, uint32_t N, uint32_t Wp, uint32_t AWp,
-                        uint32_t* P, uint32_t* aggF, uint32_t* aggU, DevStatus* st, cudaStream_t s);
+                        const uint32_t* map, uint32_t* P, uint32_t* aggF, uint32_t* aggU, DevStatus* st,
+                        cudaStream_t s);
 
-// Ingest a batch: batch offsets (n + 1, batch-relative) -> db offsets at off_db[n0 + 1 ..],
-// head planes for the new clauses, validation flags.  The batch literals are already at lits_db[L0 ..).
-cudaError_t launch_ingest(const uint64_t* boff, uint64_t n, uint64_t L, uint64_t L0, uint64_t* off_db_at_n0,
-                          uint32_t* head0_at_n0, uint32_t* head1_at_n0, const uint32_t* lits_db, uint32_t V,
-                          DevStatus* st, cudaStream_t s);
+// Ingest, in order: validate a batch (offsets -> db offsets at off_db[n0 + 1 ..], literal range);
+// on the first batch rank the variables hot-first (map[v] = internal id; scratch holds
+// rank_scratch_words(V) words); translate the batch literals through map; build head planes.
+uint64_t rank_scratch_words(uint32_t V);
+cudaError_t launch_validate(const uint64_t* boff, uint64_t n, uint64_t L, uint64_t L0, uint64_t* off_db_at_n0,
+                            const uint32_t* lits_batch, uint32_t V, DevStatus* st, cudaStream_t s);
+cudaError_t launch_rank_vars(const uint32_t* lits, uint64_t L, uint32_t V, uint32_t* scratch, uint32_t* map,
+                             cudaStream_t s);
+cudaError_t launch_translate(uint32_t* lits, uint64_t L, const uint32_t* map, cudaStream_t s);
+cudaError_t launch_build_heads(const uint64_t* boff, uint64_t n, uint64_t L0, uint32_t* head0_at_n0,
+                               uint32_t* head1_at_n0, const uint32_t* lits_db, uint32_t V, cudaStream_t s);
 
 // Test clauses [c_lo, c_hi) against the planes; append records.
 cudaError_t launch_test(int mode, const ClauseView& db, uint64_t c_lo, uint64_t c_hi, const PlaneView& pv,

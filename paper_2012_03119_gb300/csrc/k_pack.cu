@@ -48,6 +48,7 @@ constexpr uint32_t BAR_CONSUMERS = 1;              // named barrier of the consu
 struct PackSmem {
   uint8_t ring[PK_STAGES][PK_BOX];
   uint32_t stage[32 * PK_STRIDE];
+  uint32_t rowid[PK_VT];  // internal id of each variable of the current tile
   unsigned long long full[PK_STAGES], empty[PK_STAGES];
   volatile int err;
 };
@@ -72,8 +73,9 @@ __device__ __forceinline__ uint32_t stage_of(uint32_t q, uint32_t t, uint32_t w,
   return q + PK_CONSUMERS * (word_seq(q, t, w, Wd, b, g) % PK_DEPTH);
 }
 
-__global__ void __launch_bounds__(PK_THREADS, 2) k_pack(const __grid_constant__ CUtensorMap map, uint32_t V,
+__global__ void __launch_bounds__(PK_THREADS, 2) k_pack(const __grid_constant__ CUtensorMap tmap, uint32_t V,
                                                         uint32_t N, uint32_t Wp, uint32_t AWp,
+                                                        const uint32_t* __restrict__ map,
                                                         uint32_t* __restrict__ P, uint32_t* __restrict__ aggF,
                                                         uint32_t* __restrict__ aggU, DevStatus* st) {
   extern __shared__ uint8_t smem_raw[];
@@ -93,7 +95,7 @@ __global__ void __launch_bounds__(PK_THREADS, 2) k_pack(const __grid_constant__ 
 
   if (warp == PK_CONSUMERS) {  // ---------------- producer
     if (lane == 0) {
-      ptx::prefetch_tensormap(&map);
+      ptx::prefetch_tensormap(&tmap);
       uint32_t uses[PK_STAGES];  // loads issued into each stage so far
       for (int s = 0; s < PK_STAGES; ++s) uses[s] = 0u;
       bool ok = true;
@@ -105,7 +107,7 @@ __global__ void __launch_bounds__(PK_THREADS, 2) k_pack(const __grid_constant__ 
           if (uses[s] > 0u) ok = ptx::mbar_wait(&S.empty[s], (uses[s] - 1u) & 1u);  // previous use consumed
           if (!ok || S.err) { ok = false; break; }
           ptx::mbar_expect_tx(&S.full[s], PK_BOX);
-          ptx::tma_load_2d(S.ring[s], &map, (int32_t)(t * PK_VT), (int32_t)(w * PK_ROWS), &S.full[s]);
+          ptx::tma_load_2d(S.ring[s], &tmap, (int32_t)(t * PK_VT), (int32_t)(w * PK_ROWS), &S.full[s]);
           ++uses[s];
         }
       }
@@ -122,12 +124,23 @@ __global__ void __launch_bounds__(PK_THREADS, 2) k_pack(const __grid_constant__ 
 
   // ---------------- consumers
   uint32_t bad = 0;
+  // internal row ids of the next tile's variables, loaded one tile ahead (threads < PK_VT)
+  uint32_t next_row = 0;
+  if (threadIdx.x < PK_VT && blockIdx.x < n_vt) {
+    const uint32_t v = blockIdx.x * PK_VT + threadIdx.x;
+    next_row = v < V ? (map ? __ldg(map + v) : v) : 0u;
+  }
   for (uint32_t t = blockIdx.x; t < n_vt; t += gridDim.x) {
     const uint32_t v0 = t * PK_VT;
     const uint32_t nv = min((uint32_t)PK_VT, V - v0);
     for (uint32_t wc = 0; wc < Wp; wc += 32u) {
       const uint32_t nw = min(32u, Wp - wc);  // 4, 8, 16 or 32 words in this pass (one aggregate word)
       const uint32_t lg_nw = 31u - __clz(nw);
+      if (wc == 0 && threadIdx.x < PK_VT) {  // read by the write-out after the next barrier
+        S.rowid[threadIdx.x] = next_row;
+        const uint32_t v = (t + gridDim.x) * PK_VT + threadIdx.x;
+        if (t + gridDim.x < n_vt) next_row = v < V ? (map ? __ldg(map + v) : v) : 0u;
+      }
       for (uint32_t wl = warp; wl < nw; wl += PK_CONSUMERS) {
         const uint32_t w = wc + wl;
         uint32_t f[4] = {0u, 0u, 0u, 0u}, tt[4] = {0u, 0u, 0u, 0u};
@@ -188,7 +201,7 @@ __global__ void __launch_bounds__(PK_THREADS, 2) k_pack(const __grid_constant__ 
         const uint32_t bT = __ballot_sync(FULL, Tw != 0u);
         const uint32_t bU = __ballot_sync(FULL, Uw != 0u);
         if (vl < nv) {
-          const uint64_t v = v0 + vl;
+          const uint64_t v = S.rowid[vl];  // internal row of variable v0 + vl
           P[(2u * v) * Wp + w] = Fw;
           P[(2u * v + 1u) * Wp + w] = Tw;
           if (wl == 0u) {  // this variable's nw words sit in lanes [lane, lane + nw); one aggregate word per pass
@@ -221,7 +234,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }  // namespace
 
 cudaError_t launch_pack(const uint8_t* codes, uint64_t pitch, uint32_t V, uint32_t N, uint32_t Wp, uint32_t AWp,
-                        uint32_t* P, uint32_t* aggF, uint32_t* aggU, DevStatus* st, cudaStream_t s) {
+                        const uint32_t* map, uint32_t* P, uint32_t* aggF, uint32_t* aggU, DevStatus* st,
+                        cudaStream_t s) {
   // PAD literal rows 2V, 2V+1: all ones in P and aggF (neutral under AND); aggU row V: zero.
   cudaError_t e = cudaMemsetAsync(P + 2ull * V * Wp, 0xFF, 2ull * Wp * sizeof(uint32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(aggF + 2ull * V * AWp, 0xFF, 2ull * AWp * sizeof(uint32_t), s);
@@ -230,12 +244,12 @@ cudaError_t launch_pack(const uint8_t* codes, uint64_t pitch, uint32_t V, uint32
   if (pitch % 16 != 0 || reinterpret_cast<uintptr_t>(codes) % 16 != 0) return cudaErrorInvalidValue;
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
-  CUtensorMap map;
+  CUtensorMap tmap;
   const cuuint64_t dims[2] = {V, N};
   const cuuint64_t strides[1] = {pitch};
   const cuuint32_t box[2] = {PK_VT, PK_ROWS};
   const cuuint32_t estr[2] = {1, 1};
-  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(codes), dims, strides, box, estr,
+  if (enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(codes), dims, strides, box, estr,
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
@@ -248,7 +262,7 @@ cudaError_t launch_pack(const uint8_t* codes, uint64_t pitch, uint32_t V, uint32
   const uint32_t n_vt = (V + PK_VT - 1) / PK_VT;
   const uint32_t slots = 2u * (uint32_t)n_sms;  // two CTAs fit on an SM
   const uint32_t grid = n_vt < slots ? n_vt : slots;
-  k_pack<<<grid, PK_THREADS, smem, s>>>(map, V, N, Wp, AWp, P, aggF, aggU, st);
+  k_pack<<<grid, PK_THREADS, smem, s>>>(tmap, V, N, Wp, AWp, map, P, aggF, aggU, st);
   return cudaGetLastError();
 }
 

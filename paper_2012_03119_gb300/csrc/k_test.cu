@@ -17,8 +17,8 @@
 //     bit per literal (Section 4.2), ANDed (all-F) or run through the aggregateTrigger
 //     recurrence (trigger).  All gathers of a batch of literals are issued before they are
 //     combined, so a batch costs one L2 round trip.  Literals 8..15 come from head1 (one
-//     sector per clause, no offset lookup) and later ones from the CSR, only while some
-//     group is alive.  By the Theorem of Section 4.2 a group whose aggregate test fails
+//     sector per clause, no offset lookup, fetched while the first batch is tested) and
+//     later ones from the CSR, only while some group is alive.  By the Theorem of Section 4.2 a group whose aggregate test fails
 //     holds no hit;
 //   * stage B is multiTrigger's inner assignmentTrigger call: the warp's surviving
 //     (clause, group) pairs are compacted into shared memory and each lane runs the exact
@@ -29,6 +29,11 @@
 //
 // The PAD literal 2V is neutral in both modes: its P and aggF rows are all ones and its
 // aggU row is zero, so padded head slots need no branch.
+//
+// The internal variable numbering puts the hottest variables first (see k_ingest.cu); the
+// aggregate rows of the 2048 lowest literal ids (8 KiB) are copied into shared memory once
+// per block and serve most stage-A gathers under Zipf-distributed variables (the
+// shared-memory reuse of hot variables proposed in Section 7).
 #include "gss_internal.h"
 #include "gss_ptx.h"
 
@@ -39,6 +44,7 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int TEST_THREADS = 256;
 constexpr int TEST_WARPS = TEST_THREADS / 32;
 constexpr uint32_t PAIR_CAP = 64;        // candidate pairs staged per warp per round
+constexpr uint32_t HOT_WORDS = 2048;     // shared words for the hottest aggF rows (8 KiB)
 
 struct __align__(128) WarpSmem {
   uint32_t ring[2][32 * 8];  // head0 of the current and the next tile
@@ -67,6 +73,25 @@ __device__ __forceinline__ void load_agg(const uint32_t* __restrict__ base, uint
   }
 }
 
+// Aggregate row `row` (AW words): rows below n_hot come from the block's shared copy.
+template <int AW>
+__device__ __forceinline__ void load_agg_cached(const uint32_t* __restrict__ base, const uint32_t* hot, uint32_t n_hot,
+                                                uint32_t row, uint32_t (&r)[AW]) {
+  if (row < n_hot) {
+    if constexpr (AW == 1) {
+      r[0] = hot[row];
+    } else if constexpr (AW == 2) {
+      const uint2 t = reinterpret_cast<const uint2*>(hot)[row];
+      r[0] = t.x; r[1] = t.y;
+    } else {
+      const uint4 t = reinterpret_cast<const uint4*>(hot)[row];
+      r[0] = t.x; r[1] = t.y; r[2] = t.z; r[3] = t.w;
+    }
+  } else {
+    load_agg<AW>(base, row, r);
+  }
+}
+
 template <int AW>
 __device__ __forceinline__ bool any2(const uint32_t (&a)[AW], const uint32_t (&b)[AW]) {
   uint32_t o = 0;
@@ -76,15 +101,21 @@ __device__ __forceinline__ bool any2(const uint32_t (&a)[AW], const uint32_t (&b
 }
 
 // Stage A on 8 literals: gathers first, then the recurrence in order.
+struct HotRows {  // the block's shared copies of the hottest aggregate rows
+  const uint32_t* F;
+  const uint32_t* U;
+  uint32_t nF, nU;
+};
+
 template <int MODE, int AW>
-__device__ __forceinline__ void group_batch8(const PlaneView& pv, const uint32_t (&l)[8], uint32_t (&af)[AW],
-                                             uint32_t (&ou)[AW]) {
+__device__ __forceinline__ void group_batch8(const PlaneView& pv, const HotRows& hot, const uint32_t (&l)[8],
+                                             uint32_t (&af)[AW], uint32_t (&ou)[AW]) {
   constexpr int B = (AW == 4) ? 4 : 8;  // literals per sub-batch (bounds registers for wide rows)
 #pragma unroll
   for (int j0 = 0; j0 < 8; j0 += B) {
     uint32_t cf[B][AW];
 #pragma unroll
-    for (int j = 0; j < B; ++j) load_agg<AW>(pv.aggF, l[j0 + j], cf[j]);
+    for (int j = 0; j < B; ++j) load_agg_cached<AW>(pv.aggF, hot.F, hot.nF, l[j0 + j], cf[j]);
     if constexpr (MODE == GSS_MODE_ALLF) {
 #pragma unroll
       for (int j = 0; j < B; ++j)
@@ -93,7 +124,7 @@ __device__ __forceinline__ void group_batch8(const PlaneView& pv, const uint32_t
     } else {
       uint32_t cu[B][AW];
 #pragma unroll
-      for (int j = 0; j < B; ++j) load_agg<AW>(pv.aggU, l[j0 + j] >> 1, cu[j]);
+      for (int j = 0; j < B; ++j) load_agg_cached<AW>(pv.aggU, hot.U, hot.nU, l[j0 + j] >> 1, cu[j]);
 #pragma unroll
       for (int j = 0; j < B; ++j)
 #pragma unroll
@@ -188,13 +219,23 @@ template <int MODE, int AW>
 __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c_lo, uint64_t c_hi, PlaneView pv,
                                                        gss_report* __restrict__ rec, uint64_t cap, DevStatus* st) {
   __shared__ WarpSmem smem[TEST_WARPS];
+  __shared__ __align__(16) uint32_t hotF[HOT_WORDS];
+  __shared__ __align__(16) uint32_t hotU[MODE == GSS_MODE_TRIGGER ? HOT_WORDS / 2 : 4];
   if (st->bad_code) return;  // the assignment set held an invalid value code: no records
+  const uint32_t PAD = db.pad;
+  HotRows hot;
+  hot.nF = min((uint32_t)(HOT_WORDS / AW), PAD + 2u);  // literal rows 0 .. 2V + 1 exist
+  hot.nU = MODE == GSS_MODE_TRIGGER ? min((uint32_t)(HOT_WORDS / 2 / AW), PAD / 2u + 1u) : 0u;
+  for (uint32_t i = threadIdx.x; i < hot.nF * AW; i += TEST_THREADS) hotF[i] = __ldg(pv.aggF + i);
+  for (uint32_t i = threadIdx.x; i < hot.nU * AW; i += TEST_THREADS) hotU[i] = __ldg(pv.aggU + i);
+  hot.F = hotF;
+  hot.U = hotU;
+  __syncthreads();
   const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
   WarpSmem& S = smem[wib];
   const uint64_t warp_id = (uint64_t)blockIdx.x * TEST_WARPS + wib;
   const uint64_t n_warps = (uint64_t)gridDim.x * TEST_WARPS;
   const uint64_t n_tiles = (c_hi - c_lo + 31) / 32;
-  const uint32_t PAD = db.pad;
   if (warp_id >= n_tiles) return;
 
   if (lane == 0) {
@@ -238,19 +279,20 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c
 #pragma unroll
     for (int i = 0; i < AW; ++i) { af[i] = act ? FULL : 0u; ou[i] = 0u; }
     if (act) {
-      uint32_t l[8];
+      uint32_t l[8], l1[8];
       const uint4 a = reinterpret_cast<const uint4*>(h0)[0], b = reinterpret_cast<const uint4*>(h0)[1];
       l[0] = a.x; l[1] = a.y; l[2] = a.z; l[3] = a.w;
       l[4] = b.x; l[5] = b.y; l[6] = b.z; l[7] = b.w;
-      group_batch8<MODE, AW>(pv, l, af, ou);
-      if (l[7] != PAD && any2<AW>(af, ou)) {
-        load8_global(db.head1 + c * 8u, l);
-        group_batch8<MODE, AW>(pv, l, af, ou);
-        if (l[7] != PAD && any2<AW>(af, ou)) {
+      const bool long_clause = l[7] != PAD;
+      if (long_clause) load8_global(db.head1 + c * 8u, l1);  // in flight during the first batch
+      group_batch8<MODE, AW>(pv, hot, l, af, ou);
+      if (long_clause && any2<AW>(af, ou)) {
+        group_batch8<MODE, AW>(pv, hot, l1, af, ou);
+        if (l1[7] != PAD && any2<AW>(af, ou)) {
           const uint64_t e = db.off[c + 1];
           for (uint64_t k0 = db.off[c] + HEAD_K; k0 < e && any2<AW>(af, ou); k0 += 8) {
             load8_csr(db.lits, k0, e, PAD, l);
-            group_batch8<MODE, AW>(pv, l, af, ou);
+            group_batch8<MODE, AW>(pv, hot, l, af, ou);
           }
         }
       }

@@ -54,7 +54,7 @@ def test_host_only_entry_points(lib):
     assert gss.gss_strerror(-4) == "GSS_E_OVERFLOW"
     assert gss.gss_strerror(0) == "GSS_OK"
     cfg = gss.gss_config_init()
-    assert cfg.report_capacity == 1 << 22 and cfg.max_assignments == 1024 and cfg.mode == 0
+    assert cfg.report_capacity == 1 << 22 and cfg.max_assignments == 1024 and cfg.mode == 0 and cfg.layout == 1
     assert lib.gss_config_init(None) == gss.GSS_E_INVAL
     assert lib.gss_destroy(None) == 0
     assert lib.gss_last_error(None) == b"no context"

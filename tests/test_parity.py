@@ -243,3 +243,16 @@ def test_long_planted_clause():
     inst = synth.Instance("long", V, off, lits, codes, np.zeros((0, 2), np.uint32))
     got = assert_parity(inst)
     assert {0, 517, 1023} <= set(got[:, 1].tolist())
+
+
+@pytest.mark.parametrize("mode", [ALLF, TRIG])
+def test_layouts_agree(mode):
+    """The internal variable numbering changes memory layout only, never results."""
+    inst = synth.single(scale=0.01)
+    out = []
+    for layout in (gss.GSS_LAYOUT_IDENTITY, gss.GSS_LAYOUT_FREQUENCY):
+        with gss.Context(inst.n_vars, mode=mode, layout=layout, report_capacity=1 << 22) as ctx:
+            ctx.add_clauses(inst.offsets, inst.lits)
+            out.append(gss.expand_reports(ctx.run(inst.codes)))
+    assert np.array_equal(out[0], out[1])
+    assert np.array_equal(out[0], oracle.pairs(inst.offsets, inst.lits, inst.codes, mode))
