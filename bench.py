@@ -184,13 +184,85 @@ def run_reference(args, inst, workload):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+BATCH_WORKLOAD = ("batching: 64 uneven instances, 10k-2M clauses and 5k-500k vars each (log-uniform), geometric "
+                  "sizes 2 + Geom(1/7) <= 30, 128-1024 trail assignments each; one graph per run")
+
+
+def run_batch(args):
+    """Batching workload: one graph (per-instance packing + one work-stealing test launch) against
+    64 separate single-instance pack + test launches on the same GPU, same records."""
+    import torch
+    import paper_2012_03119_gb300 as gss
+    import synth
+    torch.cuda.set_device(0)
+    specs = synth.batch_specs(64, scale=args.scale)
+    insts = [synth.batch_instance(sp) for sp in specs]
+    units = sum(I.n_clauses * I.n_assign for I in insts)
+    stream = torch.cuda.Stream()
+    d_codes = [torch.from_numpy(I.codes).cuda() for I in insts]
+    caps = [I.n_clauses * ((I.n_assign + 31) // 32) // 4 + 65536 for I in insts]
+    b = gss.Batch(stream=stream)
+    for I, d, cap in zip(insts, d_codes, caps):
+        i = b.add_instance(I.n_vars, I.offsets, I.lits, max_assignments=I.n_assign, report_capacity=cap)
+        b.set_assignments(i, d)
+    ctxs = []
+    for I, cap in zip(insts, caps):
+        c = gss.Context(I.n_vars, stream=stream, report_capacity=cap, max_assignments=I.n_assign)
+        c.add_clauses(I.offsets, I.lits)
+        ctxs.append(c)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.test()  # first run: capture + autotune
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+
+    def separate():
+        for I, c, d in zip(insts, ctxs, d_codes):
+            gss.gss_set_assignments_device(c.ptr, d.data_ptr(), I.n_vars, I.n_assign)
+            c.test()
+
+    for _ in range(max(3, args.warmup)):
+        b.test()
+        separate()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        b.test()
+    ev[1].record(stream)
+    for _ in range(args.steps):
+        separate()
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    t_batch = ev[0].elapsed_time(ev[1]) / 1e3 / args.steps
+    t_sep = ev[1].elapsed_time(ev[2]) / 1e3 / args.steps
+    same = True
+    for i, c in enumerate(ctxs):  # identical records, batched and separate
+        same &= bool(np.array_equal(gss.expand_reports(b.fetch_reports(i)), gss.expand_reports(c.fetch_reports())))
+    info = b.info()
+    out = {"metric": METRIC, "value": units / t_batch / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": max(3, args.warmup), "ms_per_step": t_batch * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+           "config": {"workload": BATCH_WORKLOAD + (f" (scaled x{args.scale:g})" if args.scale != 1.0 else ""),
+                      "instances": len(insts), "clauses": int(sum(I.n_clauses for I in insts)),
+                      "pair_tests_per_step": units, "codes_resident": True},
+           "separate": {"value": units / t_sep / 1e9, "ms_per_step": t_sep * 1e3,
+                        "launches_per_step": 2 * len(insts)},
+           "speedup_vs_separate": t_sep / t_batch, "identical_records": same, "autotune": info,
+           "first_run_s": setup_s, "gpu_launches": (len(insts) + 2) * args.steps}
+    print(json.dumps(out), flush=True)
+    b.close()
+    for c in ctxs:
+        c.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gss", choices=["gss", "reference"])
-    ap.add_argument("--config", default="single", choices=["single", "structured", "tiny"])
+    ap.add_argument("--config", default="single", choices=["single", "structured", "tiny", "batch"])
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--ref-assignments", type=int, default=64)
@@ -202,6 +274,11 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.config == "batch" and args.impl != "reference":
+        if rank == 0:
+            run_batch(args)
+        return
 
     if args.impl == "reference":
         if rank != 0:

@@ -199,6 +199,68 @@ int gss_set_report_capacity(gss_ctx* ctx, uint64_t cap);
 /* Select GSS_MODE_ALLF or GSS_MODE_TRIGGER for the following gss_test calls. */
 int gss_set_mode(gss_ctx* ctx, uint32_t mode);
 
+/* ------------------------------------------------------------- batches */
+
+/*
+ * A batch: many independent clause databases ("instances"), each with its own
+ * variables, assignment set and report buffer -- e.g. the databases of several
+ * solver portfolios sharing one GPU.  Every instance is tested exactly as a
+ * context would test it (same definitions, same records); gss_batch_test runs
+ * all of them as one CUDA graph: per-instance packing on parallel branches,
+ * then one persistent launch in which warps steal 32-clause tiles of any
+ * instance from a device counter.  The graph is captured on the first test
+ * and again whenever an instance is added, the mode changes, or an instance's
+ * assignment set changes size or source buffer.  The launch shape (tiles per
+ * steal, grid) is chosen on the first test by timing candidates on the batch.
+ * Instances sharing a batch use the batch's device, stream, mode and layout.
+ */
+typedef struct gss_batch gss_batch;
+
+typedef struct {
+  uint32_t n_instances;
+  uint32_t n_groups;           /* test launches per run: one per aggregate row width */
+  uint32_t tiles_per_steal[3]; /* autotuned, per group */
+  uint32_t grid[3];            /* autotuned CTAs, per group */
+  uint64_t n_tiles[3];         /* 32-clause tiles per group */
+  uint64_t runs;               /* gss_batch_test calls */
+  float tuned_test_us;         /* test-launch time measured by the autotuner */
+} gss_batch_info;
+
+/* Create an empty batch (cfg: device, stream, mode, layout; the rest is per instance). */
+int gss_batch_create(gss_batch** out, const gss_config* cfg);
+
+/* Release the batch and every instance. */
+int gss_batch_destroy(gss_batch* b);
+
+/*
+ * Add an instance of n_vars variables holding the given clauses (as
+ * gss_add_clauses), able to take up to max_assignments assignments and to hold
+ * report_capacity records (0: the defaults of gss_config_init).  *instance_id
+ * receives its index (dense, from 0).  Synchronises the stream.
+ */
+int gss_batch_add_instance(gss_batch* b, uint32_t n_vars, uint32_t max_assignments, uint64_t report_capacity,
+                           const uint64_t* offsets, uint64_t n_clauses, const uint32_t* lits,
+                           uint32_t* instance_id);
+
+/* Stage an instance's assignment set (host codes, as gss_set_assignments); packed by gss_batch_test. */
+int gss_batch_set_assignments(gss_batch* b, uint32_t instance, const uint8_t* values, uint32_t n_assign);
+
+/* As above with device codes (as gss_set_assignments_device); the buffer must stay valid and
+ * unchanged in place until the tests that read it have run. */
+int gss_batch_set_assignments_device(gss_batch* b, uint32_t instance, const uint8_t* d_values, uint64_t pitch,
+                                     uint32_t n_assign);
+
+/* Pack and test every instance (queued on the stream).  Every instance needs an assignment
+ * set.  Errors: GSS_E_STATE, GSS_E_CUDA. */
+int gss_batch_test(gss_batch* b);
+
+/* Per-instance results of the last gss_batch_test, as gss_report_count / gss_fetch_reports. */
+int gss_batch_report_count(gss_batch* b, uint32_t instance, uint64_t* n_out);
+int gss_batch_fetch_reports(gss_batch* b, uint32_t instance, gss_report* out, uint64_t cap, uint64_t* n_out);
+
+int gss_batch_get_info(const gss_batch* b, gss_batch_info* out);
+const char* gss_batch_last_error(const gss_batch* b);
+
 /* ---------------------------------------------------------- diagnostics */
 
 int gss_get_stats(const gss_ctx* ctx, gss_stats* out);

@@ -18,7 +18,7 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["Context", "GssError", "REPORT_DTYPE", "expand_reports", "load", "GSS_MODE_ALLF", "GSS_MODE_TRIGGER"]
+__all__ = ["Batch", "Context", "GssError", "REPORT_DTYPE", "expand_reports", "load", "GSS_MODE_ALLF", "GSS_MODE_TRIGGER"]
 
 GSS_OK, GSS_E_INVAL, GSS_E_NOMEM, GSS_E_CUDA, GSS_E_OVERFLOW, GSS_E_TIMEOUT, GSS_E_BUSY, GSS_E_STATE = \
     0, -1, -2, -3, -4, -5, -6, -7
@@ -40,6 +40,12 @@ class gss_stats(ctypes.Structure):
     _fields_ = [("n_vars", ctypes.c_uint32), ("n_assign", ctypes.c_uint32), ("n_clauses", ctypes.c_uint64),
                 ("n_lits", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64), ("report_capacity", ctypes.c_uint64),
                 ("tests_run", ctypes.c_uint64), ("pair_tests", ctypes.c_uint64)]
+
+
+class gss_batch_info(ctypes.Structure):
+    _fields_ = [("n_instances", ctypes.c_uint32), ("n_groups", ctypes.c_uint32),
+                ("tiles_per_steal", ctypes.c_uint32 * 3), ("grid", ctypes.c_uint32 * 3),
+                ("n_tiles", ctypes.c_uint64 * 3), ("runs", ctypes.c_uint64), ("tuned_test_us", ctypes.c_float)]
 
 
 class GssError(RuntimeError):
@@ -72,6 +78,16 @@ SIGNATURES = {
     "gss_last_error": (ctypes.c_char_p, [P]),
     "gss_strerror": (ctypes.c_char_p, [i32]),
     "gss_version": (u32, []),
+    "gss_batch_create": (i32, [P, P]),
+    "gss_batch_destroy": (i32, [P]),
+    "gss_batch_add_instance": (i32, [P, u32, u32, u64, P, u64, P, P]),
+    "gss_batch_set_assignments": (i32, [P, u32, P, u32]),
+    "gss_batch_set_assignments_device": (i32, [P, u32, P, u64, u32]),
+    "gss_batch_test": (i32, [P]),
+    "gss_batch_report_count": (i32, [P, u32, P]),
+    "gss_batch_fetch_reports": (i32, [P, u32, P, u64, P]),
+    "gss_batch_get_info": (i32, [P, P]),
+    "gss_batch_last_error": (ctypes.c_char_p, [P]),
 }
 
 
@@ -296,3 +312,89 @@ def expand_reports(rec: np.ndarray) -> np.ndarray:
     out[:, 0] = (key >> np.uint64(32)).astype(np.uint32)
     out[:, 1] = (key & np.uint64(0xFFFFFFFF)).astype(np.uint32)
     return out
+
+
+# ---------------------------------------------------------------- batches
+class Batch:
+    """Many independent clause databases tested together (gss_batch_*): one CUDA graph per run,
+    per-instance packing on parallel branches and one work-stealing test launch."""
+
+    def __init__(self, device: int = 0, stream=None, mode: int = GSS_MODE_ALLF, layout: int = GSS_LAYOUT_FREQUENCY):
+        cfg = gss_config_init()
+        cfg.device = device
+        cfg.stream = ctypes.c_void_p(_stream_handle(stream)) if stream is not None else None
+        cfg.mode = mode
+        cfg.layout = layout
+        self._stream = stream
+        self.ptr = ctypes.c_void_p()
+        rc = load().gss_batch_create(ctypes.byref(self.ptr), ctypes.byref(cfg))
+        if rc != GSS_OK:
+            raise GssError(rc, "gss_batch_create failed")
+        self._keep = {}
+
+    def _check(self, rc):
+        if rc != GSS_OK:
+            msg = load().gss_batch_last_error(self.ptr)
+            raise GssError(rc, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            load().gss_batch_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def add_instance(self, n_vars, offsets, lits, max_assignments=1024, report_capacity=0) -> int:
+        off = np.ascontiguousarray(offsets, dtype=np.uint64)
+        lt = np.ascontiguousarray(lits, dtype=np.uint32)
+        out = ctypes.c_uint32()
+        self._check(load().gss_batch_add_instance(self.ptr, n_vars, max_assignments, report_capacity,
+                                                  ctypes.c_void_p(off.ctypes.data), len(off) - 1,
+                                                  ctypes.c_void_p(lt.ctypes.data), ctypes.byref(out)))
+        return out.value
+
+    def set_assignments(self, i: int, values) -> None:
+        ptr, keep, dev = _host_or_dev(values, np.uint8)
+        n = keep.shape[0] if keep.ndim == 2 else 0
+        if dev:
+            self._keep[i] = keep  # the graph reads it on every run
+            pitch = keep.stride(0) * keep.element_size()
+            self._check(load().gss_batch_set_assignments_device(self.ptr, i, ptr, pitch, n))
+        else:
+            self._check(load().gss_batch_set_assignments(self.ptr, i, ptr, n))
+
+    def test(self) -> None:
+        self._check(load().gss_batch_test(self.ptr))
+
+    def report_count(self, i: int) -> int:
+        n = ctypes.c_uint64()
+        self._check(load().gss_batch_report_count(self.ptr, i, ctypes.byref(n)))
+        return n.value
+
+    def fetch_reports(self, i: int) -> np.ndarray:
+        n = ctypes.c_uint64()
+        rc = load().gss_batch_fetch_reports(self.ptr, i, None, 0, ctypes.byref(n))
+        if rc not in (GSS_OK, GSS_E_OVERFLOW):
+            self._check(rc)
+        out = np.empty(n.value, dtype=REPORT_DTYPE)
+        self._check(load().gss_batch_fetch_reports(self.ptr, i, ctypes.c_void_p(out.ctypes.data), len(out),
+                                                   ctypes.byref(n)))
+        return out[: n.value]
+
+    def info(self) -> dict:
+        x = gss_batch_info()
+        self._check(load().gss_batch_get_info(self.ptr, ctypes.byref(x)))
+        k = x.n_groups
+        return {"n_instances": x.n_instances, "n_groups": k, "tiles_per_steal": list(x.tiles_per_steal)[:k],
+                "grid": list(x.grid)[:k], "n_tiles": list(x.n_tiles)[:k], "runs": x.runs,
+                "tuned_test_us": x.tuned_test_us}

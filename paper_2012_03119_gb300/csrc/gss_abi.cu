@@ -15,51 +15,13 @@
 #include <string>
 #include <unordered_map>
 
-#include "gss_internal.h"
+#include "gss_ctx.h"
 
 using namespace gss;
+using namespace gss::host;
 
-struct gss_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  uint32_t V = 0, max_N = 0, mode = GSS_MODE_ALLF, layout = GSS_LAYOUT_FREQUENCY;
-  uint64_t budget = 0, bytes = 0;
-  int n_sms = 1;
-  std::unordered_map<void*, uint64_t> allocs;
-
-  // clause database
-  uint64_t m = 0, L = 0, cap_m = 0, cap_head0 = 0, cap_head1 = 0, cap_L = 0, cap_boff = 0;
-  uint64_t* off = nullptr;
-  uint32_t* lits = nullptr;
-  uint32_t* head0 = nullptr;
-  uint32_t* head1 = nullptr;
-  uint64_t* boff = nullptr;
-  uint32_t* map = nullptr;  // internal variable ids (frequency layout), fixed by the first batch
-
-  // assignment set
-  uint32_t N = 0, Wp = 4, AWp = 1;
-  bool have_assign = false;
-  uint64_t Vp = 0;
-  uint8_t* codes = nullptr;
-  uint64_t codes_rows = 0;
-  uint32_t* P = nullptr;
-  uint32_t* aggF = nullptr;
-  uint32_t* aggU = nullptr;
-
-  // reports
-  gss_report* rec = nullptr;
-  uint64_t rec_cap = 0;
-  DevStatus* st = nullptr;    // [0]: pack + test, [1]: ingest
-  DevStatus* h_st = nullptr;  // pinned mirror
-  bool tested = false;
-  int grid[2][5] = {{0}};     // cached persistent grid per (mode, AWp)
-
-  uint64_t tests_run = 0, pair_tests = 0;
-  std::string err;
-};
-
-namespace {
+namespace gss {
+namespace host {
 
 std::atomic<long> g_alloc_counter{0};
 
@@ -194,7 +156,8 @@ void release(gss_ctx* c) {
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
-}  // namespace
+}  // namespace host
+}  // namespace gss
 
 extern "C" {
 
@@ -333,7 +296,11 @@ int gss_add_clauses(gss_ctx* c, const uint64_t* offsets, uint64_t n, const uint3
   return GSS_OK;
 }
 
-static int set_assignments_common(gss_ctx* c, const uint8_t* src, uint64_t pitch, uint32_t n, bool device_src) {
+}  // extern "C"
+
+namespace gss {
+namespace host {
+int stage_assignments(gss_ctx* c, const uint8_t* src, uint64_t pitch, uint32_t n, bool device_src) {
   if (!c) return GSS_E_INVAL;
   c->err.clear();
   if (n > c->max_N) return fail(c, GSS_E_INVAL, "n_assign %u > max_assignments %u", n, c->max_N);
@@ -367,12 +334,30 @@ static int set_assignments_common(gss_ctx* c, const uint8_t* src, uint64_t pitch
     codes = c->codes;
     cpitch = c->Vp;
   }
-  if (n) CK(c, launch_pack(codes, cpitch, c->V, n, Wp, AWp, c->map, c->P, c->aggF, c->aggU, c->st, c->stream));
+  c->pack_src = codes;
+  c->pack_pitch = cpitch;
   c->N = n;
   c->Wp = Wp;
   c->AWp = AWp;
   c->have_assign = true;
   return GSS_OK;
+}
+
+int pack_staged(gss_ctx* c, cudaStream_t s) {
+  if (c->N) CK(c, launch_pack(c->pack_src, c->pack_pitch, c->V, c->N, c->Wp, c->AWp, c->map, c->P, c->aggF, c->aggU,
+                              c->st, s));
+  return GSS_OK;
+}
+}  // namespace host
+}  // namespace gss
+
+extern "C" {
+
+static int set_assignments_common(gss_ctx* c, const uint8_t* src, uint64_t pitch, uint32_t n, bool device_src) {
+  int rc = stage_assignments(c, src, pitch, n, device_src);
+  if (rc) return rc;
+  DeviceGuard dg(c->device);
+  return pack_staged(c, c->stream);
 }
 
 int gss_set_assignments(gss_ctx* c, const uint8_t* values, uint32_t n_assign) {
@@ -401,9 +386,13 @@ int gss_test(gss_ctx* c) {
   return GSS_OK;
 }
 
-static int wait_test(gss_ctx* c, uint64_t* n) {
+}  // extern "C"
+
+namespace gss {
+namespace host {
+int wait_test(gss_ctx* c, uint64_t* n, bool sync) {
   if (!c->tested) return fail(c, GSS_E_STATE, "no gss_test to fetch");
-  int rc = sync_status(c);
+  int rc = sync ? sync_status(c) : GSS_OK;
   if (rc) return rc;
   if (c->h_st[0].bad_code) {
     *n = 0;
@@ -416,13 +405,17 @@ static int wait_test(gss_ctx* c, uint64_t* n) {
   *n = c->h_st[0].n_records;
   return GSS_OK;
 }
+}  // namespace host
+}  // namespace gss
+
+extern "C" {
 
 int gss_fetch_reports(gss_ctx* c, gss_report* out, uint64_t cap, uint64_t* n_out) {
   if (!c || (cap && !out)) return c ? fail(c, GSS_E_INVAL, "out is NULL") : GSS_E_INVAL;
   c->err.clear();
   DeviceGuard dg(c->device);
   uint64_t n = 0;
-  int rc = wait_test(c, &n);
+  int rc = wait_test(c, &n, true);
   if (n_out) *n_out = n;
   if (rc) return rc;
   uint64_t k = n < cap ? n : cap;
@@ -445,7 +438,7 @@ int gss_report_count(gss_ctx* c, uint64_t* n_out) {
   if (!c || !n_out) return GSS_E_INVAL;
   c->err.clear();
   DeviceGuard dg(c->device);
-  int rc = wait_test(c, n_out);
+  int rc = wait_test(c, n_out, true);
   if (rc) return rc;
   if (*n_out > c->rec_cap)
     return fail(c, GSS_E_OVERFLOW, "device report buffer overflowed: %llu records > capacity %llu",

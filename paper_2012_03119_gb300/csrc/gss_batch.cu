@@ -1,0 +1,443 @@
+// gss_batch.cu -- host side of the batch ABI (include/gss.h, "batches").
+//
+// A batch holds many independent clause databases ("instances"), each with its own
+// assignment set and report buffer -- the independent problems of a multi-solver
+// deployment.  One gss_batch_test runs a CUDA graph captured once per batch layout:
+//   1. reset the work counters and every instance's test status;
+//   2. pack every instance's assignment set (one packing kernel per instance, on parallel
+//      branches of the graph so small instances run side by side);
+//   3. test every clause of every instance in ONE persistent launch per row width (AWp)
+//      in which warps steal 32-clause tiles from a device counter (k_test_batch).
+// The launch shape of step 3 (tiles per steal, grid size) is chosen by timing candidates
+// on the batch itself the first time it runs (gss_batch_get_tuning reports the choice).
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gss_ctx.h"
+
+using namespace gss;
+using namespace gss::host;
+
+namespace {
+
+constexpr int SIDE_STREAMS = 8;
+
+struct Group {  // instances sharing one aggregate row width
+  uint32_t awp = 1;
+  std::vector<uint32_t> members;
+  uint64_t n_tiles = 0;
+  BatchInst* d_inst = nullptr;
+  unsigned long long* work = nullptr;
+  uint32_t grab = 4;
+  int grid = 0;
+};
+
+struct Captured {  // what the graph baked in for one instance
+  const uint8_t* src;
+  uint64_t pitch;
+  uint32_t N, Wp;
+};
+
+}  // namespace
+
+struct gss_batch {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  uint32_t mode = GSS_MODE_ALLF, layout = GSS_LAYOUT_FREQUENCY;
+  int n_sms = 1;
+  std::vector<gss_ctx*> inst;
+  std::vector<Captured> captured;
+  std::vector<Group> groups;
+  DevStatus* bst = nullptr;
+  DevStatus* h_bst = nullptr;
+  cudaStream_t side[SIDE_STREAMS] = {};
+  cudaEvent_t fork = nullptr, join[SIDE_STREAMS] = {};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool dirty = true, tuned = false;
+  float tuned_us = 0.f;
+  uint64_t runs = 0;
+  std::string err;
+};
+
+namespace {
+
+int bfail(gss_batch* b, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (b) b->err = buf;
+  return code;
+}
+
+#define BCK(b, call)                                                                              \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return bfail((b), GSS_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+struct Guard {
+  int prev = -1;
+  bool changed = false;
+  explicit Guard(int d) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != d) changed = cudaSetDevice(d) == cudaSuccess;
+  }
+  ~Guard() {
+    if (changed && prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+void drop_graph(gss_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+void drop_groups(gss_batch* b) {
+  for (Group& g : b->groups) {
+    if (g.d_inst) cudaFree(g.d_inst);
+    if (g.work) cudaFree(g.work);
+  }
+  b->groups.clear();
+}
+
+int child_fail(gss_batch* b, gss_ctx* c, int rc) { return bfail(b, rc, "%s", gss_last_error(c)); }
+
+// Descriptor tables, one group per aggregate row width.
+int build_groups(gss_batch* b) {
+  drop_groups(b);
+  for (uint32_t i = 0; i < b->inst.size(); ++i) {
+    gss_ctx* c = b->inst[i];
+    if (!c->have_assign) return bfail(b, GSS_E_STATE, "instance %u has no assignment set", i);
+    Group* g = nullptr;
+    for (Group& x : b->groups)
+      if (x.awp == c->AWp) g = &x;
+    if (!g) {
+      b->groups.emplace_back();
+      g = &b->groups.back();
+      g->awp = c->AWp;
+    }
+    g->members.push_back(i);
+  }
+  for (Group& g : b->groups) {
+    std::vector<BatchInst> h;
+    uint64_t tiles = 0;
+    for (uint32_t i : g.members) {
+      gss_ctx* c = b->inst[i];
+      BatchInst d{};
+      d.db = ClauseView{c->off, c->lits, c->head0, c->head1, 2u * c->V};
+      d.pv = PlaneView{c->P, c->aggF, c->aggU, c->Wp, c->AWp, c->N};
+      d.m = c->N ? c->m : 0;  // an empty assignment set has nothing to test
+      d.tile0 = tiles;
+      d.rec = c->rec;
+      d.cap = c->rec_cap;
+      d.st = c->st;
+      tiles += (d.m + 31) / 32;
+      h.push_back(d);
+    }
+    g.n_tiles = tiles;
+    BCK(b, cudaMalloc(&g.d_inst, h.size() * sizeof(BatchInst)));
+    BCK(b, cudaMalloc(&g.work, sizeof(unsigned long long)));
+    BCK(b, cudaMemcpyAsync(g.d_inst, h.data(), h.size() * sizeof(BatchInst), cudaMemcpyHostToDevice, b->stream));
+    g.grid = test_batch_grid_size((int)b->mode, g.awp, b->n_sms);
+  }
+  BCK(b, cudaStreamSynchronize(b->stream));
+  return GSS_OK;
+}
+
+int enqueue_resets(gss_batch* b, cudaStream_t s) {
+  for (Group& g : b->groups)
+    BCK(b, launch_batch_reset(g.d_inst, (uint32_t)g.members.size(), g.work, b->bst, s));
+  return GSS_OK;
+}
+
+int enqueue_tests(gss_batch* b, cudaStream_t s) {
+  for (Group& g : b->groups)
+    BCK(b, launch_test_batch((int)b->mode, g.awp, g.d_inst, (uint32_t)g.members.size(), g.n_tiles, g.work, g.grab,
+                             b->bst, g.grid, s));
+  return GSS_OK;
+}
+
+int enqueue_packs(gss_batch* b) {  // on the side streams, forked from and joined into b->stream
+  BCK(b, cudaEventRecord(b->fork, b->stream));
+  for (int k = 0; k < SIDE_STREAMS; ++k) BCK(b, cudaStreamWaitEvent(b->side[k], b->fork, 0));
+  for (uint32_t i = 0; i < b->inst.size(); ++i) {
+    int rc = pack_staged(b->inst[i], b->side[i % SIDE_STREAMS]);
+    if (rc) return child_fail(b, b->inst[i], rc);
+  }
+  for (int k = 0; k < SIDE_STREAMS; ++k) {
+    BCK(b, cudaEventRecord(b->join[k], b->side[k]));
+    BCK(b, cudaStreamWaitEvent(b->stream, b->join[k], 0));
+  }
+  return GSS_OK;
+}
+
+// Time (tiles per steal, grid) candidates for each group's test launch; keep the fastest.
+int autotune(gss_batch* b) {
+  int rc;
+  if ((rc = enqueue_resets(b, b->stream)) || (rc = enqueue_packs(b))) return rc;
+  cudaEvent_t e0, e1;
+  BCK(b, cudaEventCreate(&e0));
+  BCK(b, cudaEventCreate(&e1));
+  float total = 0.f;
+  for (Group& g : b->groups) {
+    const int full = g.grid;
+    const uint32_t grabs[] = {1, 2, 4, 8, 16};
+    const int grids[] = {full, full / 2 > 0 ? full / 2 : 1};
+    float best = 1e30f;
+    uint32_t best_grab = 4;
+    int best_grid = full;
+    for (int gd : grids)
+      for (uint32_t gr : grabs) {
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+          BCK(b, launch_batch_reset(g.d_inst, (uint32_t)g.members.size(), g.work, b->bst, b->stream));
+          BCK(b, cudaEventRecord(e0, b->stream));
+          BCK(b, launch_test_batch((int)b->mode, g.awp, g.d_inst, (uint32_t)g.members.size(), g.n_tiles, g.work, gr,
+                                   b->bst, gd, b->stream));
+          BCK(b, cudaEventRecord(e1, b->stream));
+          BCK(b, cudaEventSynchronize(e1));
+          float ms = 0.f;
+          BCK(b, cudaEventElapsedTime(&ms, e0, e1));
+          if (ms < ms_min) ms_min = ms;
+        }
+        if (ms_min < best) {
+          best = ms_min;
+          best_grab = gr;
+          best_grid = gd;
+        }
+      }
+    g.grab = best_grab;
+    g.grid = best_grid;
+    total += best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->tuned_us = total * 1e3f;
+  b->tuned = true;
+  return GSS_OK;
+}
+
+int capture(gss_batch* b) {
+  drop_graph(b);
+  BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  int rc = enqueue_resets(b, b->stream);
+  if (!rc) rc = enqueue_packs(b);
+  if (!rc) rc = enqueue_tests(b, b->stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return bfail(b, GSS_E_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  b->graph = g;
+  BCK(b, cudaGraphInstantiate(&b->exec, b->graph, 0));
+  b->captured.clear();
+  for (gss_ctx* c : b->inst) b->captured.push_back(Captured{c->pack_src, c->pack_pitch, c->N, c->Wp});
+  b->dirty = false;
+  return GSS_OK;
+}
+
+bool still_captured(gss_batch* b, uint32_t i) {
+  if (b->dirty || i >= b->captured.size()) return false;
+  const gss_ctx* c = b->inst[i];
+  const Captured& k = b->captured[i];
+  return k.src == c->pack_src && k.pitch == c->pack_pitch && k.N == c->N && k.Wp == c->Wp;
+}
+
+gss_ctx* instance(gss_batch* b, uint32_t i) { return i < b->inst.size() ? b->inst[i] : nullptr; }
+
+}  // namespace
+
+extern "C" {
+
+int gss_batch_create(gss_batch** out, const gss_config* cfg_in) {
+  if (!out) return GSS_E_INVAL;
+  *out = nullptr;
+  gss_config cfg;
+  if (cfg_in) cfg = *cfg_in; else gss_config_init(&cfg);
+  if (cfg.mode != GSS_MODE_ALLF && cfg.mode != GSS_MODE_TRIGGER) return GSS_E_INVAL;
+  if (cfg.layout != GSS_LAYOUT_IDENTITY && cfg.layout != GSS_LAYOUT_FREQUENCY) return GSS_E_INVAL;
+  int n_dev = 0;
+  if (cudaGetDeviceCount(&n_dev) != cudaSuccess || cfg.device < 0 || cfg.device >= n_dev) {
+    cudaGetLastError();
+    return GSS_E_CUDA;
+  }
+  gss_batch* b = new (std::nothrow) gss_batch();
+  if (!b) return GSS_E_NOMEM;
+  Guard gd(cfg.device);
+  b->device = cfg.device;
+  b->mode = cfg.mode;
+  b->layout = cfg.layout;
+  if (cudaDeviceGetAttribute(&b->n_sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess) b->n_sms = 1;
+  bool ok = true;
+  if (cfg.stream) {
+    b->stream = static_cast<cudaStream_t>(cfg.stream);
+  } else {
+    ok = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess;
+    b->own_stream = ok;
+  }
+  for (int k = 0; ok && k < SIDE_STREAMS; ++k) {
+    ok = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming) == cudaSuccess;
+  }
+  ok = ok && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->bst, sizeof(DevStatus)) == cudaSuccess;
+  ok = ok && cudaMallocHost(&b->h_bst, sizeof(DevStatus)) == cudaSuccess;
+  ok = ok && cudaMemset(b->bst, 0, sizeof(DevStatus)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    gss_batch_destroy(b);
+    return GSS_E_CUDA;
+  }
+  *out = b;
+  return GSS_OK;
+}
+
+int gss_batch_destroy(gss_batch* b) {
+  if (!b) return GSS_OK;
+  Guard gd(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  drop_graph(b);
+  drop_groups(b);
+  for (gss_ctx* c : b->inst) gss_destroy(c);
+  for (int k = 0; k < SIDE_STREAMS; ++k) {
+    if (b->side[k]) cudaStreamDestroy(b->side[k]);
+    if (b->join[k]) cudaEventDestroy(b->join[k]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->bst) cudaFree(b->bst);
+  if (b->h_bst) cudaFreeHost(b->h_bst);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return GSS_OK;
+}
+
+int gss_batch_add_instance(gss_batch* b, uint32_t n_vars, uint32_t max_assignments, uint64_t report_capacity,
+                           const uint64_t* offsets, uint64_t n_clauses, const uint32_t* lits, uint32_t* instance_id) {
+  if (!b) return GSS_E_INVAL;
+  b->err.clear();
+  gss_config cfg;
+  gss_config_init(&cfg);
+  cfg.device = b->device;
+  cfg.stream = b->stream;
+  cfg.mode = b->mode;
+  cfg.layout = b->layout;
+  if (max_assignments) cfg.max_assignments = max_assignments;
+  if (report_capacity) cfg.report_capacity = report_capacity;
+  gss_ctx* c = nullptr;
+  int rc = gss_create(&c, n_vars, &cfg);
+  if (rc) return bfail(b, rc, "instance creation failed (n_vars %u, max_assignments %u)", n_vars, max_assignments);
+  rc = gss_add_clauses(c, offsets, n_clauses, lits, nullptr);
+  if (rc) {
+    bfail(b, rc, "%s", gss_last_error(c));
+    gss_destroy(c);
+    return rc;
+  }
+  if (instance_id) *instance_id = (uint32_t)b->inst.size();
+  b->inst.push_back(c);
+  b->dirty = true;
+  return GSS_OK;
+}
+
+int gss_batch_set_assignments(gss_batch* b, uint32_t i, const uint8_t* values, uint32_t n_assign) {
+  if (!b) return GSS_E_INVAL;
+  gss_ctx* c = instance(b, i);
+  if (!c) return bfail(b, GSS_E_INVAL, "no instance %u", i);
+  Guard gd(b->device);
+  int rc = stage_assignments(c, values, 0, n_assign, false);
+  if (rc) return child_fail(b, c, rc);
+  if (!still_captured(b, i)) b->dirty = true;
+  return GSS_OK;
+}
+
+int gss_batch_set_assignments_device(gss_batch* b, uint32_t i, const uint8_t* d_values, uint64_t pitch,
+                                     uint32_t n_assign) {
+  if (!b) return GSS_E_INVAL;
+  gss_ctx* c = instance(b, i);
+  if (!c) return bfail(b, GSS_E_INVAL, "no instance %u", i);
+  Guard gd(b->device);
+  int rc = stage_assignments(c, d_values, pitch, n_assign, true);
+  if (rc) return child_fail(b, c, rc);
+  if (!still_captured(b, i)) b->dirty = true;
+  return GSS_OK;
+}
+
+int gss_batch_test(gss_batch* b) {
+  if (!b) return GSS_E_INVAL;
+  b->err.clear();
+  if (b->inst.empty()) return bfail(b, GSS_E_STATE, "the batch has no instances");
+  Guard gd(b->device);
+  int rc;
+  if (b->dirty) {
+    if ((rc = build_groups(b))) return rc;
+    if (!b->tuned && (rc = autotune(b))) return rc;
+    if ((rc = capture(b))) return rc;
+  }
+  BCK(b, cudaGraphLaunch(b->exec, b->stream));
+  for (gss_ctx* c : b->inst) {
+    c->tested = true;
+    c->tests_run += 1;
+    c->pair_tests += c->m * (uint64_t)c->N;
+  }
+  b->runs += 1;
+  return GSS_OK;
+}
+
+int gss_batch_report_count(gss_batch* b, uint32_t i, uint64_t* n_out) {
+  if (!b || !n_out) return GSS_E_INVAL;
+  gss_ctx* c = instance(b, i);
+  if (!c) return bfail(b, GSS_E_INVAL, "no instance %u", i);
+  Guard gd(b->device);
+  BCK(b, cudaMemcpyAsync(b->h_bst, b->bst, sizeof(DevStatus), cudaMemcpyDeviceToHost, b->stream));
+  BCK(b, cudaStreamSynchronize(b->stream));
+  if (b->h_bst->timeout) return bfail(b, GSS_E_TIMEOUT, "a bounded device wait gave up during the batched test");
+  int rc = gss_report_count(c, n_out);
+  return rc ? child_fail(b, c, rc) : GSS_OK;
+}
+
+int gss_batch_fetch_reports(gss_batch* b, uint32_t i, gss_report* out, uint64_t cap, uint64_t* n_out) {
+  if (!b) return GSS_E_INVAL;
+  gss_ctx* c = instance(b, i);
+  if (!c) return bfail(b, GSS_E_INVAL, "no instance %u", i);
+  Guard gd(b->device);
+  BCK(b, cudaMemcpyAsync(b->h_bst, b->bst, sizeof(DevStatus), cudaMemcpyDeviceToHost, b->stream));
+  BCK(b, cudaStreamSynchronize(b->stream));
+  if (b->h_bst->timeout) return bfail(b, GSS_E_TIMEOUT, "a bounded device wait gave up during the batched test");
+  int rc = gss_fetch_reports(c, out, cap, n_out);
+  return rc ? child_fail(b, c, rc) : GSS_OK;
+}
+
+int gss_batch_get_info(const gss_batch* b, gss_batch_info* out) {
+  if (!b || !out) return GSS_E_INVAL;
+  memset(out, 0, sizeof *out);
+  out->n_instances = (uint32_t)b->inst.size();
+  out->runs = b->runs;
+  out->tuned_test_us = b->tuned_us;
+  uint32_t k = 0;
+  for (const Group& g : b->groups) {
+    if (k >= 3) break;
+    out->tiles_per_steal[k] = g.grab;
+    out->grid[k] = (uint32_t)g.grid;
+    out->n_tiles[k] = g.n_tiles;
+    ++k;
+  }
+  out->n_groups = k;
+  return GSS_OK;
+}
+
+const char* gss_batch_last_error(const gss_batch* b) { return b ? b->err.c_str() : "no batch"; }
+
+}  // extern "C"

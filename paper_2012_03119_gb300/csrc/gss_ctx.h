@@ -1,0 +1,72 @@
+// gss_ctx.h -- the context behind the C ABI, shared by the single-instance (gss_abi.cu)
+// and batch (gss_batch.cu) host code.  Not part of the public interface.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <unordered_map>
+
+#include "gss_internal.h"
+
+using gss::DevStatus;
+
+struct gss_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  uint32_t V = 0, max_N = 0, mode = GSS_MODE_ALLF, layout = GSS_LAYOUT_FREQUENCY;
+  uint64_t budget = 0, bytes = 0;
+  int n_sms = 1;
+  std::unordered_map<void*, uint64_t> allocs;
+
+  // clause database
+  uint64_t m = 0, L = 0, cap_m = 0, cap_head0 = 0, cap_head1 = 0, cap_L = 0, cap_boff = 0;
+  uint64_t* off = nullptr;
+  uint32_t* lits = nullptr;
+  uint32_t* head0 = nullptr;
+  uint32_t* head1 = nullptr;
+  uint64_t* boff = nullptr;
+  uint32_t* map = nullptr;  // internal variable ids (frequency layout), fixed by the first batch
+
+  // assignment set
+  uint32_t N = 0, Wp = 4, AWp = 1;
+  bool have_assign = false;
+  uint64_t Vp = 0;
+  uint8_t* codes = nullptr;
+  uint64_t codes_rows = 0;
+  uint32_t* P = nullptr;
+  uint32_t* aggF = nullptr;
+  uint32_t* aggU = nullptr;
+  const uint8_t* pack_src = nullptr;  // codes the next packing reads (staging buffer or caller memory)
+  uint64_t pack_pitch = 0;
+
+  // reports
+  gss_report* rec = nullptr;
+  uint64_t rec_cap = 0;
+  DevStatus* st = nullptr;    // [0]: pack + test, [1]: ingest
+  DevStatus* h_st = nullptr;  // pinned mirror
+  bool tested = false;
+  int grid[2][5] = {{0}};     // cached persistent grid per (mode, AWp)
+
+  uint64_t tests_run = 0, pair_tests = 0;
+  std::string err;
+};
+
+namespace gss {
+namespace host {
+
+int fail(gss_ctx* c, int code, const char* fmt, ...);
+int dev_alloc(gss_ctx* c, void** p, uint64_t bytes);
+void dev_free(gss_ctx* c, void* p);
+int sync_status(gss_ctx* c);
+uint32_t words_stride(uint32_t N);
+uint32_t agg_stride(uint32_t Wp);
+// Copy / register an assignment set without packing it (the batch packs inside its graph).
+int stage_assignments(gss_ctx* c, const uint8_t* src, uint64_t pitch, uint32_t n, bool device_src);
+// Pack the staged assignment set on stream s.
+int pack_staged(gss_ctx* c, cudaStream_t s);
+// Wait for the last test of c and read its record count (status already synchronised when sync = false).
+int wait_test(gss_ctx* c, uint64_t* n, bool sync);
+
+}  // namespace host
+}  // namespace gss

@@ -79,4 +79,24 @@ cudaError_t launch_test(int mode, const ClauseView& db, uint64_t c_lo, uint64_t 
 // Occupancy-derived persistent grid for launch_test on this device.
 int test_grid_size(int mode, uint32_t AWp, int n_sms);
 
+// One instance of a batch as the batched test kernel sees it.
+struct BatchInst {
+  ClauseView db;
+  PlaneView pv;
+  uint64_t m;      // clauses
+  uint64_t tile0;  // index of the instance's first 32-clause tile among all the batch's tiles
+  gss_report* rec;
+  uint64_t cap;
+  DevStatus* st;   // the instance's test status (records, bad codes)
+};
+
+// Zero the work counter, the batch status and each instance's test status.
+cudaError_t launch_batch_reset(const BatchInst* d_inst, uint32_t n_inst, unsigned long long* work, DevStatus* bst,
+                               cudaStream_t s);
+// Test every instance (all with the same AWp) in one persistent launch; warps take `grab`
+// tiles at a time from the device counter *work (zeroed by launch_batch_reset).
+cudaError_t launch_test_batch(int mode, uint32_t AWp, const BatchInst* d_inst, uint32_t n_inst, uint64_t n_tiles,
+                              unsigned long long* work, uint32_t grab, DevStatus* bst, int grid, cudaStream_t s);
+int test_batch_grid_size(int mode, uint32_t AWp, int n_sms);
+
 }  // namespace gss

@@ -254,10 +254,14 @@ cudaError_t launch_pack(const uint8_t* codes, uint64_t pitch, uint32_t V, uint32
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
   const size_t smem = sizeof(PackSmem) + 128;
-  e = cudaFuncSetAttribute(k_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   int dev = 0, n_sms = 1;
   cudaGetDevice(&dev);
+  static bool smem_set[64] = {};  // once per device, before any graph capture that packs
+  if (dev < 0 || dev >= 64 || !smem_set[dev]) {
+    e = cudaFuncSetAttribute(k_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) smem_set[dev] = true;
+  }
   cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev);
   const uint32_t n_vt = (V + PK_VT - 1) / PK_VT;
   const uint32_t slots = 2u * (uint32_t)n_sms;  // two CTAs fit on an SM

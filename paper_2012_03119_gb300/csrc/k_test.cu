@@ -215,6 +215,83 @@ __device__ __forceinline__ void warp_append(bool has, uint32_t c, uint32_t g, ui
   }
 }
 
+// Stage A and stage B for the tile of clauses [c0, min(c0 + 32, c_hi)), whose head0 is in
+// S.ring[s]; records go to rec / n_records.
+template <int MODE, int AW>
+__device__ __forceinline__ void test_tile(const ClauseView& db, const PlaneView& pv, const HotRows& hot, WarpSmem& S,
+                                          int s, uint64_t c0, uint64_t c_hi, uint32_t lane,
+                                          gss_report* __restrict__ rec, uint64_t cap, unsigned long long* n_records) {
+  const uint32_t PAD = db.pad;
+  const uint64_t c = c0 + lane;
+  const bool act = c < c_hi;
+  const uint32_t* h0 = &S.ring[s][lane * 8u];
+
+  // ---------------- stage A: group (aggregate) test of this lane's clause
+  uint32_t af[AW], ou[AW];
+#pragma unroll
+  for (int i = 0; i < AW; ++i) { af[i] = act ? FULL : 0u; ou[i] = 0u; }
+  if (act) {
+    uint32_t l[8], l1[8];
+    const uint4 a = reinterpret_cast<const uint4*>(h0)[0], b = reinterpret_cast<const uint4*>(h0)[1];
+    l[0] = a.x; l[1] = a.y; l[2] = a.z; l[3] = a.w;
+    l[4] = b.x; l[5] = b.y; l[6] = b.z; l[7] = b.w;
+    const bool long_clause = l[7] != PAD;
+    if (long_clause) load8_global(db.head1 + c * 8u, l1);  // in flight during the first batch
+    group_batch8<MODE, AW>(pv, hot, l, af, ou);
+    if (long_clause && any2<AW>(af, ou)) {
+      group_batch8<MODE, AW>(pv, hot, l1, af, ou);
+      if (l1[7] != PAD && any2<AW>(af, ou)) {
+        const uint64_t e = db.off[c + 1];
+        for (uint64_t k0 = db.off[c] + HEAD_K; k0 < e && any2<AW>(af, ou); k0 += 8) {
+          load8_csr(db.lits, k0, e, PAD, l);
+          group_batch8<MODE, AW>(pv, hot, l, af, ou);
+        }
+      }
+    }
+  }
+  uint32_t cand[AW];
+#pragma unroll
+  for (int i = 0; i < AW; ++i) cand[i] = af[i] | ou[i];
+
+  // ---------------- stage B: exact test of the warp's candidate (clause, group) pairs
+  for (;;) {
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int i = 0; i < AW; ++i) cnt += __popc(cand[i]);
+    const uint32_t total = __reduce_add_sync(FULL, cnt);
+    if (total == 0u) break;
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, incl, d);
+      if (lane >= (uint32_t)d) incl += y;
+    }
+    uint32_t pos = incl - cnt;
+#pragma unroll
+    for (int i = 0; i < AW; ++i) {
+      while (cand[i] != 0u && pos < PAIR_CAP) {
+        const uint32_t bit = (uint32_t)(__ffs(cand[i]) - 1);
+        cand[i] &= cand[i] - 1u;
+        S.pairs[pos++] = lane | ((32u * i + bit) << 5);
+      }
+    }
+    __syncwarp();
+    const uint32_t np = total < PAIR_CAP ? total : PAIR_CAP;
+    for (uint32_t p0 = 0; p0 < np; p0 += 32u) {
+      const uint32_t p = p0 + lane;
+      uint32_t res = 0u, g = 0u, owner = 0u;
+      if (p < np) {
+        const uint32_t e = S.pairs[p];
+        owner = e & 31u;
+        g = e >> 5;
+        res = exact_pair<MODE>(db, pv, c0 + owner, &S.ring[s][owner * 8u], g);
+      }
+      warp_append(res != 0u, (uint32_t)(c0 + owner), g, res, lane, rec, cap, n_records);
+    }
+    __syncwarp();
+  }
+}
+
 template <int MODE, int AW>
 __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c_lo, uint64_t c_hi, PlaneView pv,
                                                        gss_report* __restrict__ rec, uint64_t cap, DevStatus* st) {
@@ -269,77 +346,103 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c
       __syncwarp();
       return;
     }
-    const uint64_t c0 = c_lo + t * 32u;
-    const uint64_t c = c0 + lane;
-    const bool act = c < c_hi;
-    const uint32_t* h0 = &S.ring[s][lane * 8u];
-
-    // ---------------- stage A: group (aggregate) test of this lane's clause
-    uint32_t af[AW], ou[AW];
-#pragma unroll
-    for (int i = 0; i < AW; ++i) { af[i] = act ? FULL : 0u; ou[i] = 0u; }
-    if (act) {
-      uint32_t l[8], l1[8];
-      const uint4 a = reinterpret_cast<const uint4*>(h0)[0], b = reinterpret_cast<const uint4*>(h0)[1];
-      l[0] = a.x; l[1] = a.y; l[2] = a.z; l[3] = a.w;
-      l[4] = b.x; l[5] = b.y; l[6] = b.z; l[7] = b.w;
-      const bool long_clause = l[7] != PAD;
-      if (long_clause) load8_global(db.head1 + c * 8u, l1);  // in flight during the first batch
-      group_batch8<MODE, AW>(pv, hot, l, af, ou);
-      if (long_clause && any2<AW>(af, ou)) {
-        group_batch8<MODE, AW>(pv, hot, l1, af, ou);
-        if (l1[7] != PAD && any2<AW>(af, ou)) {
-          const uint64_t e = db.off[c + 1];
-          for (uint64_t k0 = db.off[c] + HEAD_K; k0 < e && any2<AW>(af, ou); k0 += 8) {
-            load8_csr(db.lits, k0, e, PAD, l);
-            group_batch8<MODE, AW>(pv, hot, l, af, ou);
-          }
-        }
-      }
-    }
-    uint32_t cand[AW];
-#pragma unroll
-    for (int i = 0; i < AW; ++i) cand[i] = af[i] | ou[i];
-
-    // ---------------- stage B: exact test of the warp's candidate (clause, group) pairs
-    for (;;) {
-      uint32_t cnt = 0;
-#pragma unroll
-      for (int i = 0; i < AW; ++i) cnt += __popc(cand[i]);
-      const uint32_t total = __reduce_add_sync(FULL, cnt);
-      if (total == 0u) break;
-      uint32_t incl = cnt;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(FULL, incl, d);
-        if (lane >= (uint32_t)d) incl += y;
-      }
-      uint32_t pos = incl - cnt;
-#pragma unroll
-      for (int i = 0; i < AW; ++i) {
-        while (cand[i] != 0u && pos < PAIR_CAP) {
-          const uint32_t bit = (uint32_t)(__ffs(cand[i]) - 1);
-          cand[i] &= cand[i] - 1u;
-          S.pairs[pos++] = lane | ((32u * i + bit) << 5);
-        }
-      }
-      __syncwarp();
-      const uint32_t np = total < PAIR_CAP ? total : PAIR_CAP;
-      for (uint32_t p0 = 0; p0 < np; p0 += 32u) {
-        const uint32_t p = p0 + lane;
-        uint32_t res = 0u, g = 0u, owner = 0u;
-        if (p < np) {
-          const uint32_t e = S.pairs[p];
-          owner = e & 31u;
-          g = e >> 5;
-          res = exact_pair<MODE>(db, pv, c0 + owner, &S.ring[s][owner * 8u], g);
-        }
-        warp_append(res != 0u, (uint32_t)(c0 + owner), g, res, lane, rec, cap, &st->n_records);
-      }
-      __syncwarp();
-    }
+    test_tile<MODE, AW>(db, pv, hot, S, s, c_lo + t * 32u, c_hi, lane, rec, cap, &st->n_records);
     __syncwarp();
   }
+}
+
+// Last instance whose first tile is <= t (instances without clauses are skipped because a
+// later instance starts at the same tile).
+__device__ __forceinline__ uint32_t find_inst(const BatchInst* __restrict__ inst, uint32_t n, uint64_t t) {
+  uint32_t lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) / 2;
+    if (__ldg(&inst[mid].tile0) <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// One persistent launch over the 32-clause tiles of every instance of a batch.  Warps take
+// `grab` consecutive tiles at a time from a device counter (work stealing), so instances of
+// very different sizes share the GPU without a launch each; the head0 copy of a warp's next
+// tile is in flight while the current one is tested, as in k_test.
+template <int MODE, int AW>
+__global__ void __launch_bounds__(TEST_THREADS) k_test_batch(const BatchInst* __restrict__ inst, uint32_t n_inst,
+                                                             uint64_t n_tiles, unsigned long long* __restrict__ work,
+                                                             uint32_t grab, DevStatus* bst) {
+  __shared__ WarpSmem smem[TEST_WARPS];
+  const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+  WarpSmem& S = smem[wib];
+  HotRows hot;  // rows differ between instances: no shared copy
+  hot.F = hot.U = nullptr;
+  hot.nF = hot.nU = 0;
+  unsigned long long cb = 0;
+  if (lane == 0) cb = atomicAdd(work, (unsigned long long)grab);
+  cb = __shfl_sync(FULL, cb, 0);
+  if (cb >= n_tiles) return;
+  uint64_t ce = min((uint64_t)cb + grab, n_tiles);
+  if (lane == 0) {
+    ptx::mbar_init(&S.bar[0], 1);
+    ptx::mbar_init(&S.bar[1], 1);
+    ptx::fence_mbar_init();
+  }
+  __syncwarp();
+  auto issue = [&](uint64_t t, int stage) {  // lane 0: bulk-copy tile t's head0 into ring[stage]
+    const BatchInst& d = inst[find_inst(inst, n_inst, t)];
+    const uint64_t c0 = (t - d.tile0) * 32u;
+    const uint64_t left = d.m - c0;
+    const uint32_t n = left < 32u ? (uint32_t)left : 32u;
+    ptx::fence_proxy_async();
+    ptx::mbar_expect_tx(&S.bar[stage], n * 32u);
+    ptx::bulk_g2s(S.ring[stage], d.db.head0 + c0 * 8u, n * 32u, &S.bar[stage]);
+  };
+  uint64_t t = cb;
+  if (lane == 0) issue(t, 0);
+  for (uint32_t it = 0;; ++it) {
+    uint64_t tn = t + 1;
+    if (tn >= ce) {  // take the next chunk of tiles
+      unsigned long long nb = 0;
+      if (lane == 0) nb = atomicAdd(work, (unsigned long long)grab);
+      tn = __shfl_sync(FULL, nb, 0);
+      ce = min(tn + grab, n_tiles);
+    }
+    const bool has_next = tn < n_tiles;
+    const int s = it & 1;
+    if (lane == 0 && has_next) issue(tn, s ^ 1);
+    const bool ok = ptx::mbar_wait(&S.bar[s], (it >> 1) & 1u);
+    if (!__all_sync(FULL, ok)) {  // bounded wait gave up: flag it, drain our copies (bounded), leave
+      if (lane == 0) {
+        atomicOr(&bst->timeout, 1u);
+        ptx::mbar_wait(&S.bar[s], (it >> 1) & 1u);
+        if (has_next) ptx::mbar_wait(&S.bar[s ^ 1], ((it + 1) >> 1) & 1u);
+      }
+      __syncwarp();
+      return;
+    }
+    const uint32_t i = find_inst(inst, n_inst, t);
+    const ClauseView db = inst[i].db;
+    const PlaneView pv = inst[i].pv;
+    DevStatus* st = inst[i].st;
+    if (!st->bad_code)
+      test_tile<MODE, AW>(db, pv, hot, S, s, (t - inst[i].tile0) * 32u, inst[i].m, lane, inst[i].rec, inst[i].cap,
+                          &st->n_records);
+    __syncwarp();  // every lane is done with ring[s] before it is refilled
+    if (!has_next) break;
+    t = tn;
+  }
+}
+
+// Zero the work counter, the batch status and every instance's test status (records, bad
+// codes, timeouts) before a batched run.
+__global__ void k_batch_reset(const BatchInst* __restrict__ inst, uint32_t n_inst, unsigned long long* work,
+                              DevStatus* bst) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    *work = 0ull;
+    *bst = DevStatus{};
+  }
+  if (i < n_inst) *inst[i].st = DevStatus{};
 }
 
 template <int MODE, int AW>
@@ -357,7 +460,52 @@ int grid_for(int n_sms) {
   return per_sm * n_sms;
 }
 
+template <int MODE, int AW>
+int batch_grid_for(int n_sms) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_test_batch<MODE, AW>, TEST_THREADS, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return per_sm * n_sms;
+}
+
 }  // namespace
+
+cudaError_t launch_batch_reset(const BatchInst* d_inst, uint32_t n_inst, unsigned long long* work, DevStatus* bst,
+                               cudaStream_t s) {
+  k_batch_reset<<<(n_inst + 255) / 256 + 1, 256, 0, s>>>(d_inst, n_inst, work, bst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_test_batch(int mode, uint32_t AWp, const BatchInst* d_inst, uint32_t n_inst, uint64_t n_tiles,
+                              unsigned long long* work, uint32_t grab, DevStatus* bst, int grid, cudaStream_t s) {
+  if (n_inst == 0 || n_tiles == 0) return cudaSuccess;
+  if (grid < 1) grid = 1;
+  if (grab < 1) grab = 1;
+#define GSS_BATCH_LAUNCH(M, A) k_test_batch<M, A><<<grid, TEST_THREADS, 0, s>>>(d_inst, n_inst, n_tiles, work, grab, bst)
+  if (mode == GSS_MODE_ALLF) {
+    if (AWp == 1) GSS_BATCH_LAUNCH(GSS_MODE_ALLF, 1);
+    else if (AWp == 2) GSS_BATCH_LAUNCH(GSS_MODE_ALLF, 2);
+    else GSS_BATCH_LAUNCH(GSS_MODE_ALLF, 4);
+  } else {
+    if (AWp == 1) GSS_BATCH_LAUNCH(GSS_MODE_TRIGGER, 1);
+    else if (AWp == 2) GSS_BATCH_LAUNCH(GSS_MODE_TRIGGER, 2);
+    else GSS_BATCH_LAUNCH(GSS_MODE_TRIGGER, 4);
+  }
+#undef GSS_BATCH_LAUNCH
+  return cudaGetLastError();
+}
+
+int test_batch_grid_size(int mode, uint32_t AWp, int n_sms) {
+  if (mode == GSS_MODE_ALLF) {
+    if (AWp == 1) return batch_grid_for<GSS_MODE_ALLF, 1>(n_sms);
+    if (AWp == 2) return batch_grid_for<GSS_MODE_ALLF, 2>(n_sms);
+    return batch_grid_for<GSS_MODE_ALLF, 4>(n_sms);
+  }
+  if (AWp == 1) return batch_grid_for<GSS_MODE_TRIGGER, 1>(n_sms);
+  if (AWp == 2) return batch_grid_for<GSS_MODE_TRIGGER, 2>(n_sms);
+  return batch_grid_for<GSS_MODE_TRIGGER, 4>(n_sms);
+}
 
 cudaError_t launch_test(int mode, const ClauseView& db, uint64_t c_lo, uint64_t c_hi, const PlaneView& pv,
                         gss_report* rec, uint64_t cap, DevStatus* st, int grid, cudaStream_t s) {
