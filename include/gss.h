@@ -261,6 +261,48 @@ int gss_batch_fetch_reports(gss_batch* b, uint32_t instance, gss_report* out, ui
 int gss_batch_get_info(const gss_batch* b, gss_batch_info* out);
 const char* gss_batch_last_error(const gss_batch* b);
 
+/* ------------------------------------------------- without allocation */
+
+/*
+ * Size of the fixed device array gss_test_noalloc works in (32 MiB).  The paper has no
+ * counterpart to this entry point; it exists for callers that cannot allocate.
+ */
+#define GSS_NOALLOC_SCRATCH_BYTES (32ull << 20)
+
+/*
+ * The whole test -- validation, clause heads, packing, testing, record compaction --
+ * for callers that must not allocate device memory while they run it: a program whose
+ * GPU memory belongs to another runtime's pool, or a loop that cannot afford the device
+ * synchronisation a cudaMalloc may cause.  The caller provides every input and output
+ * in device memory on the current device; the function allocates nothing (no cudaMalloc,
+ * no library allocator).  Its working memory is one array of GSS_NOALLOC_SCRATCH_BYTES
+ * compiled into the library, which every GPU that loads the library holds until the
+ * process exits.
+ *   d_offsets, n_clauses, d_lits  the clauses, as gss_add_clauses but in device memory
+ *   n_vars                        V (literals 2v + s < 2V)
+ *   d_values, pitch, n_assign     value codes as gss_set_assignments_device; here the
+ *                                 pointer and pitch must be multiples of 16
+ *   mode                          GSS_MODE_ALLF or GSS_MODE_TRIGGER
+ *   d_out, cap                    record buffer (gss_report, record order unspecified)
+ *   d_count                       device counter that receives the number of records
+ *   stream                        cudaStream_t to work on (NULL: the legacy default stream)
+ *   errbuf, errbuf_len            optional host buffer for a message (nullable)
+ * Results equal those of gss_add_clauses + gss_set_assignments_device + gss_test on a
+ * context (the caller's variable numbering is kept).  The call returns when the results
+ * are in d_out / d_count (it synchronises the stream).  Problems whose working memory
+ * (about 72 bytes per clause plus 8 (Wp + 1.5 AWp) bytes per variable, Wp = N/32 rounded up to a power of
+ * two >= 4) exceeds GSS_NOALLOC_SCRATCH_BYTES are rejected with GSS_E_INVAL and a
+ * message; larger problems go through a context.  Errors otherwise as gss_add_clauses,
+ * gss_test and gss_fetch_reports (GSS_E_OVERFLOW: *d_count holds the full count).
+ * Every call on a device reuses the same array and leaves its contents behind, so calls
+ * that may overlap on the GPU (other streams, other host threads) must not be issued:
+ * they would race on it.  The first call on a device looks up the array's device address
+ * (with that device current); make that first call before any stream capture.
+ */
+int gss_test_noalloc(const uint64_t* d_offsets, uint64_t n_clauses, const uint32_t* d_lits, uint32_t n_vars,
+                     const uint8_t* d_values, uint64_t pitch, uint32_t n_assign, uint32_t mode, gss_report* d_out,
+                     uint64_t cap, unsigned long long* d_count, void* stream, char* errbuf, size_t errbuf_len);
+
 /* ---------------------------------------------------------- diagnostics */
 
 int gss_get_stats(const gss_ctx* ctx, gss_stats* out);

@@ -88,6 +88,7 @@ SIGNATURES = {
     "gss_batch_fetch_reports": (i32, [P, u32, P, u64, P]),
     "gss_batch_get_info": (i32, [P, P]),
     "gss_batch_last_error": (ctypes.c_char_p, [P]),
+    "gss_test_noalloc": (i32, [P, u64, P, u32, P, u64, u32, u32, P, u64, P, P, P, ctypes.c_size_t]),
 }
 
 
@@ -215,6 +216,18 @@ def gss_reports_device(ctx) -> tuple[int, int]:
     cap = ctypes.c_uint64()
     _check(ctx, load().gss_reports_device(ctx, ctypes.byref(p), ctypes.byref(cap)))
     return p.value or 0, cap.value
+
+
+def gss_test_noalloc(d_offsets: int, n_clauses: int, d_lits: int, n_vars: int, d_values: int, pitch: int,
+                     n_assign: int, mode: int, d_out: int, cap: int, d_count: int, stream: int = 0) -> None:
+    """The whole test on caller-owned device buffers, allocating nothing (see include/gss.h).
+    Arguments are device addresses (ints); raises GssError on failure."""
+    buf = ctypes.create_string_buffer(256)
+    rc = load().gss_test_noalloc(ctypes.c_void_p(d_offsets), n_clauses, ctypes.c_void_p(d_lits), n_vars,
+                                 ctypes.c_void_p(d_values), pitch, n_assign, mode, ctypes.c_void_p(d_out), cap,
+                                 ctypes.c_void_p(d_count), ctypes.c_void_p(stream), buf, len(buf))
+    if rc != GSS_OK:
+        raise GssError(rc, buf.value.decode())
 
 
 def gss_strerror(code: int) -> str:
