@@ -256,17 +256,190 @@ def run_batch(args):
         c.close()
 
 
+SERVE_WORKLOAD = ("serving: 1M vars, resident DB grows 2M -> 6M clauses (80 batches of 50k, one per 50 ms), "
+                  "geometric sizes 2 + Geom(1/7) <= 30, Zipf(1.1) vars; 32 simulated solver threads submit "
+                  "32-assignment trail snapshots (40-60% assigned), Poisson arrivals 2k req/s in total")
+
+
+def run_serve(args):
+    """Serving workload: an open-loop phase (Poisson arrivals while the database grows) for
+    latency and achieved tests/s, then a closed-loop phase on the final database comparing the
+    server's saturated throughput with one pack + test launch per request through a context."""
+    import threading
+    import torch
+    import paper_2012_03119_gb300 as gss
+    import synth
+    torch.cuda.set_device(0)
+    w = synth.serve_workload(scale=args.scale)
+    V, final = w.n_vars, len(w.offsets) - 1
+    n_pool = 32  # distinct snapshots, cycled by the clients (pinned, as a solver's own buffers would be)
+    pool_t = torch.empty((n_pool, 32, V), dtype=torch.uint8, pin_memory=True)
+    pool = pool_t.numpy()
+    pool[:] = synth.serve_snapshots(V, n_pool, seed=synth.seed_for(4, 1))
+    cap = 1 << 23
+    srv = gss.Server(V, max_clauses=final + 1, max_lits=int(w.offsets[-1]) + 1, slots=64, lanes=3,
+                     lane_report_capacity=cap)
+    srv.add_clauses(*w.csr(0, w.n_initial))
+    for i in range(max(3, args.warmup)):
+        srv.wait(srv.submit(pool[i], wait_us=10_000_000))
+
+    n_threads, rate = args.serve_threads, args.serve_rate
+    period = 0.05
+    lock = threading.Lock()
+    done = []  # (watermark, n_assign, records, latency_us, batch_words)
+    drops = [0]
+    errors = []
+    t_start = time.perf_counter() + 0.05
+    t_end = t_start + w.n_batches * period
+
+    def keep(r):
+        rec, info = r
+        with lock:
+            done.append((info["watermark"], info["n_assign"], len(rec), info["latency_us"], info["batch_words"]))
+
+    def client(t):
+        try:
+            rng = np.random.default_rng(1000 + t)
+            nxt = t_start + rng.exponential(n_threads / rate)
+            pending, j = [], 0
+            while nxt < t_end:
+                dt = nxt - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                rid = srv.submit(pool[(7 * t + j) % n_pool], wait_us=0)  # not sent when the GPU is full
+                j += 1
+                if rid is None:
+                    with lock:
+                        drops[0] += 1
+                else:
+                    pending.append(rid)
+                still = []
+                for q in pending:
+                    r = srv.wait(q, wait_us=0)
+                    if r is None:
+                        still.append(q)
+                    else:
+                        keep(r)
+                pending = still
+                nxt += rng.exponential(n_threads / rate)
+            for q in pending:
+                keep(srv.wait(q))
+        except Exception as e:
+            errors.append(e)
+
+    def ingest():
+        try:
+            for b in range(w.n_batches):
+                dt = t_start + b * period - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                srv.add_clauses(*w.csr(*w.batch_range(b)))
+        except Exception as e:
+            errors.append(e)
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    s0 = srv.stats()
+    ths = [threading.Thread(target=ingest)] + [threading.Thread(target=client, args=(t,)) for t in range(n_threads)]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    t_open = time.perf_counter() - t_start
+    s1 = srv.stats()
+    if errors:
+        raise errors[0]
+    lat = np.array([d[3] for d in done])
+    tests_open = sum(d[0] * d[1] for d in done)
+
+    # closed loop on the final database: every client keeps one request in flight
+    n_sat = args.serve_sat_requests
+    sat_recs = {}
+
+    def sat_client(t):
+        try:
+            for j in range(t, n_sat, n_threads):
+                rec, info = srv.wait(srv.submit(pool[j % n_pool], wait_us=10_000_000))
+                if j < n_pool:
+                    with lock:
+                        sat_recs[j] = rec
+        except Exception as e:
+            errors.append(e)
+
+    s2 = srv.stats()
+    t0 = time.perf_counter()
+    ths = [threading.Thread(target=sat_client, args=(t,)) for t in range(n_threads)]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    t_sat = time.perf_counter() - t0
+    s3 = srv.stats()
+    if errors:
+        raise errors[0]
+    srv.close()
+
+    # one pack + test launch per request (host codes, as the server receives them)
+    ctx = gss.Context(V, max_assignments=32, report_capacity=cap)
+    ctx.add_clauses(w.offsets, w.lits)
+    n_one = min(n_sat, 4 * n_pool)
+    same = True
+    for j in range(3):
+        ctx.set_assignments(pool[j])
+        ctx.test()
+        ctx.fetch_reports()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j in range(n_one):
+        ctx.set_assignments(pool[j % n_pool])
+        ctx.test()
+        rec = ctx.fetch_reports()
+        if j in sat_recs:
+            same &= bool(np.array_equal(gss.expand_reports(rec), gss.expand_reports(sat_recs[j])))
+    t_one = time.perf_counter() - t0
+    ctx.close()
+    clk = clocks.stop()
+
+    sat_tests = float(final) * 32 * n_sat
+    out = {"metric": METRIC, "value": tests_open / t_open / 1e9, "unit": UNIT, "n_gpus": 1,
+           "steps": len(done), "warmup": max(3, args.warmup), "ms_per_step": t_open * 1e3 / max(1, len(done)),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+           "config": {"workload": SERVE_WORKLOAD + (f" (scaled x{args.scale:g})" if args.scale != 1.0 else ""),
+                      "threads": n_threads, "rate_req_s": rate, "snapshot_pool": n_pool, "slots": s1["slots"],
+                      "lanes": 3, "final_clauses": final},
+           "open_loop": {"seconds": t_open, "requests": len(done), "dropped": drops[0],
+                         "launches": s1["launches"] - s0["launches"],
+                         "mean_batch_words": (s1["words_launched"] - s0["words_launched"]) /
+                         max(1, s1["launches"] - s0["launches"]),
+                         "latency_us": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                                        "max": float(lat.max()), "mean": float(lat.mean())},
+                         "records": int(sum(d[2] for d in done)), "req_per_s": len(done) / t_open},
+           "saturated": {"requests": n_sat, "seconds": t_sat, "req_per_s": n_sat / t_sat,
+                         "G_tests_s": sat_tests / t_sat / 1e9,
+                         "mean_batch_words": (s3["words_launched"] - s2["words_launched"]) /
+                         max(1, s3["launches"] - s2["launches"])},
+           "one_launch_per_request": {"requests": n_one, "req_per_s": n_one / t_one,
+                                      "G_tests_s": float(final) * 32 * n_one / t_one / 1e9},
+           "speedup_vs_one_launch_per_request": (n_sat / t_sat) / (n_one / t_one),
+           "identical_records": same, "clocks": clk,
+           "gpu_launches": 3 * (s3["launches"] - s0["launches"])}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gss", choices=["gss", "reference"])
-    ap.add_argument("--config", default="single", choices=["single", "structured", "tiny", "batch"])
+    ap.add_argument("--config", default="single", choices=["single", "structured", "tiny", "batch", "serve"])
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--ref-assignments", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="requests/s over all simulated solver threads")
+    ap.add_argument("--serve-threads", type=int, default=32)
+    ap.add_argument("--serve-sat-requests", type=int, default=1024)
     ap.add_argument("--layout", default="frequency", choices=["frequency", "identity"],
                     help="internal variable numbering of the clause database")
     args = ap.parse_args()
@@ -278,6 +451,10 @@ def main():
     if args.config == "batch" and args.impl != "reference":
         if rank == 0:
             run_batch(args)
+        return
+    if args.config == "serve" and args.impl != "reference":
+        if rank == 0:
+            run_serve(args)
         return
 
     if args.impl == "reference":

@@ -46,7 +46,7 @@ enum {
   GSS_E_NOMEM = -2,     /* device allocation failed or the memory budget is exhausted */
   GSS_E_CUDA = -3,      /* a CUDA runtime call failed (message in gss_last_error) */
   GSS_E_OVERFLOW = -4,  /* more report records than the buffer given (count still returned) */
-  GSS_E_TIMEOUT = -5,   /* a bounded device-side wait gave up */
+  GSS_E_TIMEOUT = -5,   /* a bounded wait gave up (device side, or gss_server_wait) */
   GSS_E_BUSY = -6,      /* no free slot (serving admission) */
   GSS_E_STATE = -7      /* call out of order (e.g. gss_test before gss_set_assignments) */
 };
@@ -302,6 +302,107 @@ const char* gss_batch_last_error(const gss_batch* b);
 int gss_test_noalloc(const uint64_t* d_offsets, uint64_t n_clauses, const uint32_t* d_lits, uint32_t n_vars,
                      const uint8_t* d_values, uint64_t pitch, uint32_t n_assign, uint32_t mode, gss_report* d_out,
                      uint64_t cap, unsigned long long* d_count, void* stream, char* errbuf, size_t errbuf_len);
+
+/* ------------------------------------------------------------- serving */
+
+/*
+ * A server keeps one clause database resident on the device while solver threads stream
+ * in learned clauses and submit assignment snapshots (Section 3.6: each CPU thread sends
+ * the parent assignment of its conflicts and every clause it learns; the GPU tests all of
+ * its clauses against the assignments not yet tested and reports the hits to the thread
+ * that sent the assignment; assignments are not sent when the GPU is full).
+ *
+ * A request is a snapshot of 1 to 32 assignments (one plane word).  It is admitted into
+ * one of a fixed number of device slots; when none frees up within the caller's wait the
+ * submission is refused with GSS_E_BUSY (memory admission).  Admitted requests that are
+ * not yet on the GPU join the next launch: a scheduler thread keeps up to `lanes` launches
+ * in flight, each testing the clause database against up to 32 requests at once.
+ *
+ * Each request tests the clauses with id < its watermark: the number of clauses committed
+ * when it was admitted (or a smaller value the caller asks for).  Its records therefore do
+ * not depend on the other requests of its launch nor on clauses added later.  Records use
+ * the caller's clause ids (in order of gss_server_add_clauses) and word 0; bit b of mask is
+ * assignment b of the request.
+ *
+ * Threads: gss_server_add_clauses, gss_server_submit and gss_server_wait may be called from
+ * any number of host threads; the database may grow while launches run.
+ */
+typedef struct gss_server gss_server;
+
+typedef struct {
+  int device;                    /* CUDA device ordinal */
+  uint32_t mode;                 /* GSS_MODE_ALLF or GSS_MODE_TRIGGER */
+  uint32_t layout;               /* GSS_LAYOUT_*; frequency numbering is fixed by the first clause batch */
+  uint64_t max_clauses;          /* clause capacity reserved at creation (the database never moves) */
+  uint64_t max_lits;             /* literal capacity reserved at creation */
+  uint32_t slots;                /* request slots, 32 * ceil16(n_vars) bytes of device memory each */
+  uint32_t lanes;                /* launches in flight at once (1 to 8) */
+  uint64_t lane_report_capacity; /* records one launch can hold; more fail the launch's requests */
+  uint64_t slot_memory_bytes;    /* non-zero: slots = min(slots, slot_memory_bytes / slot size) */
+} gss_server_config;
+
+/* Flags of gss_server_submit. */
+#define GSS_SUBMIT_KEEP 1u /* keep the records for gss_server_wait (otherwise only counted) */
+
+/* Watermark meaning "every clause committed at admission". */
+#define GSS_WATERMARK_ALL 0xFFFFFFFFFFFFFFFFull
+
+typedef struct {
+  uint64_t watermark;  /* clauses the request was tested against: ids [0, watermark) */
+  uint32_t n_assign;
+  uint32_t batch_words; /* requests in the launch that carried it */
+  double latency_us;    /* from the start of gss_server_submit to results on the host */
+} gss_request_info;
+
+typedef struct {
+  uint64_t submitted, dropped, completed; /* dropped: refused with GSS_E_BUSY */
+  uint64_t launches, words_launched;      /* launches and the requests they carried */
+  uint64_t pair_tests;                    /* sum over completed requests of watermark * n_assign */
+  uint64_t reports;                       /* records delivered (after dropping padded assignments) */
+  uint64_t committed_clauses;
+  uint32_t slots, pad;
+  double p50_us, p99_us, max_us, mean_us; /* latency of completed requests */
+} gss_server_stats;
+
+int gss_server_config_init(gss_server_config* cfg);
+
+/* Create a server for n_vars variables; reserves the database and request slots and starts
+ * the scheduler thread.  GSS_E_NOMEM if the reservation does not fit. */
+int gss_server_create(gss_server** out, uint32_t n_vars, const gss_server_config* cfg);
+
+/* Stop the scheduler (launches in flight finish first) and free everything. */
+int gss_server_destroy(gss_server* srv);
+
+/* Append clauses as gss_add_clauses (host CSR).  They are visible to requests admitted
+ * after the call returns.  GSS_E_NOMEM when the reserved capacity would be exceeded. */
+int gss_server_add_clauses(gss_server* srv, const uint64_t* offsets, uint64_t n_clauses, const uint32_t* lits,
+                           uint32_t* first_id);
+
+/*
+ * Submit a request: values holds n_assign (1..32) rows of n_vars codes (0 = U, 1 = T,
+ * 2 = F), row-major, in host memory; it may be reused when the call returns.  watermark
+ * caps the clauses tested (GSS_WATERMARK_ALL: all committed ones).  wait_us: how long to
+ * wait for a free slot (0: refuse at once with GSS_E_BUSY).  *request_id identifies the
+ * request for gss_server_wait when flags has GSS_SUBMIT_KEEP.
+ */
+int gss_server_submit(gss_server* srv, const uint8_t* values, uint32_t n_assign, uint64_t watermark, int64_t wait_us,
+                      uint32_t flags, uint64_t* request_id);
+
+/*
+ * Wait up to wait_us (negative: without limit) for a kept request and take its records
+ * into out (*n_out = their number; records in no particular order).  With more than cap
+ * records nothing is copied, *n_out holds the count, GSS_E_OVERFLOW is returned and the
+ * request is kept: call again with a larger buffer.  Otherwise the request is forgotten
+ * afterwards unless the result is GSS_E_TIMEOUT (not finished yet).  GSS_E_OVERFLOW with
+ * records copied: the launch's record buffer overflowed and the records are incomplete.
+ * GSS_E_INVAL: a code outside {0, 1, 2} was in the request's launch.  One waiter per
+ * request.  info (nullable) receives the watermark, batch size and latency.
+ */
+int gss_server_wait(gss_server* srv, uint64_t request_id, int64_t wait_us, gss_report* out, uint64_t cap,
+                    uint64_t* n_out, gss_request_info* info);
+
+int gss_server_get_stats(gss_server* srv, gss_server_stats* out);
+const char* gss_server_last_error(const gss_server* srv);
 
 /* ---------------------------------------------------------- diagnostics */
 

@@ -18,13 +18,15 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["Batch", "Context", "GssError", "REPORT_DTYPE", "expand_reports", "load", "GSS_MODE_ALLF", "GSS_MODE_TRIGGER"]
+__all__ = ["Batch", "Context", "Server", "GssError", "REPORT_DTYPE", "expand_reports", "load", "GSS_MODE_ALLF", "GSS_MODE_TRIGGER"]
 
 GSS_OK, GSS_E_INVAL, GSS_E_NOMEM, GSS_E_CUDA, GSS_E_OVERFLOW, GSS_E_TIMEOUT, GSS_E_BUSY, GSS_E_STATE = \
     0, -1, -2, -3, -4, -5, -6, -7
 GSS_MODE_ALLF, GSS_MODE_TRIGGER = 0, 1
 GSS_LAYOUT_IDENTITY, GSS_LAYOUT_FREQUENCY = 0, 1
 GSS_MAX_ASSIGNMENTS = 4096
+GSS_SUBMIT_KEEP = 1
+GSS_WATERMARK_ALL = 0xFFFFFFFFFFFFFFFF
 GSS_HEAD_WIDTH = 16
 
 REPORT_DTYPE = np.dtype([("clause_id", "<u4"), ("word", "<u4"), ("mask", "<u4")])
@@ -46,6 +48,26 @@ class gss_batch_info(ctypes.Structure):
     _fields_ = [("n_instances", ctypes.c_uint32), ("n_groups", ctypes.c_uint32),
                 ("tiles_per_steal", ctypes.c_uint32 * 3), ("grid", ctypes.c_uint32 * 3),
                 ("n_tiles", ctypes.c_uint64 * 3), ("runs", ctypes.c_uint64), ("tuned_test_us", ctypes.c_float)]
+
+
+class gss_server_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("mode", ctypes.c_uint32), ("layout", ctypes.c_uint32),
+                ("max_clauses", ctypes.c_uint64), ("max_lits", ctypes.c_uint64), ("slots", ctypes.c_uint32),
+                ("lanes", ctypes.c_uint32), ("lane_report_capacity", ctypes.c_uint64),
+                ("slot_memory_bytes", ctypes.c_uint64)]
+
+
+class gss_request_info(ctypes.Structure):
+    _fields_ = [("watermark", ctypes.c_uint64), ("n_assign", ctypes.c_uint32), ("batch_words", ctypes.c_uint32),
+                ("latency_us", ctypes.c_double)]
+
+
+class gss_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("dropped", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("launches", ctypes.c_uint64), ("words_launched", ctypes.c_uint64), ("pair_tests", ctypes.c_uint64),
+                ("reports", ctypes.c_uint64), ("committed_clauses", ctypes.c_uint64), ("slots", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32), ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
+                ("max_us", ctypes.c_double), ("mean_us", ctypes.c_double)]
 
 
 class GssError(RuntimeError):
@@ -89,6 +111,14 @@ SIGNATURES = {
     "gss_batch_get_info": (i32, [P, P]),
     "gss_batch_last_error": (ctypes.c_char_p, [P]),
     "gss_test_noalloc": (i32, [P, u64, P, u32, P, u64, u32, u32, P, u64, P, P, P, ctypes.c_size_t]),
+    "gss_server_config_init": (i32, [P]),
+    "gss_server_create": (i32, [P, u32, P]),
+    "gss_server_destroy": (i32, [P]),
+    "gss_server_add_clauses": (i32, [P, P, u64, P, P]),
+    "gss_server_submit": (i32, [P, P, u32, u64, ctypes.c_int64, u32, P]),
+    "gss_server_wait": (i32, [P, u64, ctypes.c_int64, P, u64, P, P]),
+    "gss_server_get_stats": (i32, [P, P]),
+    "gss_server_last_error": (ctypes.c_char_p, [P]),
 }
 
 
@@ -411,3 +441,94 @@ class Batch:
         return {"n_instances": x.n_instances, "n_groups": k, "tiles_per_steal": list(x.tiles_per_steal)[:k],
                 "grid": list(x.grid)[:k], "n_tiles": list(x.n_tiles)[:k], "runs": x.runs,
                 "tuned_test_us": x.tuned_test_us}
+
+
+# ---------------------------------------------------------------- serving
+class Server:
+    """A resident, growing clause database serving 32-assignment requests (gss_server_*):
+    slot admission, a scheduler thread batching the waiting requests into overlapping
+    launches, per-request watermarks.  Methods may be called from several threads (the
+    library releases the GIL inside each call)."""
+
+    def __init__(self, n_vars: int, device: int = 0, mode: int = GSS_MODE_ALLF, layout: int = GSS_LAYOUT_FREQUENCY,
+                 max_clauses: int = 1 << 20, max_lits: int = 1 << 24, slots: int = 64, lanes: int = 3,
+                 lane_report_capacity: int = 1 << 20, slot_memory_bytes: int = 0):
+        cfg = gss_server_config()
+        load().gss_server_config_init(ctypes.byref(cfg))
+        cfg.device, cfg.mode, cfg.layout = device, mode, layout
+        cfg.max_clauses, cfg.max_lits, cfg.slots, cfg.lanes = max_clauses, max_lits, slots, lanes
+        cfg.lane_report_capacity, cfg.slot_memory_bytes = lane_report_capacity, slot_memory_bytes
+        self.n_vars = n_vars
+        self.ptr = ctypes.c_void_p()
+        rc = load().gss_server_create(ctypes.byref(self.ptr), n_vars, ctypes.byref(cfg))
+        if rc != GSS_OK:
+            self.ptr = None
+            raise GssError(rc, "gss_server_create failed")
+
+    def _check(self, rc):
+        if rc != GSS_OK:
+            msg = load().gss_server_last_error(self.ptr)
+            raise GssError(rc, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            load().gss_server_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def add_clauses(self, offsets, lits) -> int:
+        off = np.ascontiguousarray(offsets, dtype=np.uint64)
+        lt = np.ascontiguousarray(lits, dtype=np.uint32)
+        out = ctypes.c_uint32()
+        self._check(load().gss_server_add_clauses(self.ptr, ctypes.c_void_p(off.ctypes.data), len(off) - 1,
+                                                  ctypes.c_void_p(lt.ctypes.data), ctypes.byref(out)))
+        return out.value
+
+    def submit(self, values, watermark: int | None = None, wait_us: int = 0, keep: bool = True) -> int | None:
+        """Submit rows of value codes (host, [n <= 32][n_vars] uint8).  Returns the request id,
+        or None when no slot freed up within wait_us (GSS_E_BUSY)."""
+        ptr, arr, dev = _host_or_dev(values, np.uint8)
+        if dev:
+            raise ValueError("requests are host memory")
+        if arr.ndim != 2 or arr.shape[1] != self.n_vars:
+            raise ValueError(f"values must be [n_assign][{self.n_vars}]")
+        rid = ctypes.c_uint64()
+        wm = GSS_WATERMARK_ALL if watermark is None else watermark
+        rc = load().gss_server_submit(self.ptr, ptr, arr.shape[0], wm, wait_us, GSS_SUBMIT_KEEP if keep else 0,
+                                      ctypes.byref(rid))
+        if rc == GSS_E_BUSY:
+            return None
+        self._check(rc)
+        return rid.value
+
+    def wait(self, request_id: int, wait_us: int = -1):
+        """Records (REPORT_DTYPE, word 0) and info of a kept request; None if not finished in wait_us."""
+        n = ctypes.c_uint64()
+        info = gss_request_info()
+        out = np.empty(64, dtype=REPORT_DTYPE)
+        while True:
+            rc = load().gss_server_wait(self.ptr, request_id, wait_us, ctypes.c_void_p(out.ctypes.data), len(out),
+                                        ctypes.byref(n), ctypes.byref(info))
+            if rc == GSS_E_TIMEOUT:
+                return None
+            if rc == GSS_E_OVERFLOW and n.value > len(out):
+                out = np.empty(n.value, dtype=REPORT_DTYPE)
+                continue
+            self._check(rc)
+            return out[: n.value].copy(), {k: getattr(info, k) for k, _ in info._fields_}
+
+    def stats(self) -> dict:
+        x = gss_server_stats()
+        self._check(load().gss_server_get_stats(self.ptr, ctypes.byref(x)))
+        return {k: getattr(x, k) for k, _ in x._fields_ if k != "pad"}

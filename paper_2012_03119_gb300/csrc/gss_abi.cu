@@ -300,6 +300,18 @@ int gss_add_clauses(gss_ctx* c, const uint64_t* offsets, uint64_t n, const uint3
 
 namespace gss {
 namespace host {
+int reserve_db(gss_ctx* c, uint64_t max_clauses, uint64_t max_lits) {
+  if (!c) return GSS_E_INVAL;
+  if (max_clauses >= (1ull << 32)) return fail(c, GSS_E_INVAL, "more than 2^32 - 1 clauses");
+  DeviceGuard dg(c->device);
+  int rc;
+  if ((rc = grow(c, c->off, c->cap_m, c->m + 1, max_clauses + 1))) return rc;
+  if ((rc = grow(c, c->head0, c->cap_head0, c->m * 8, max_clauses * 8))) return rc;
+  if ((rc = grow(c, c->head1, c->cap_head1, c->m * 8, max_clauses * 8))) return rc;
+  if ((rc = grow(c, c->lits, c->cap_L, c->L, max_lits ? max_lits : 1))) return rc;
+  return GSS_OK;
+}
+
 int stage_assignments(gss_ctx* c, const uint8_t* src, uint64_t pitch, uint32_t n, bool device_src) {
   if (!c) return GSS_E_INVAL;
   c->err.clear();

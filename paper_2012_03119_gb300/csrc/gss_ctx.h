@@ -65,6 +65,9 @@ uint32_t agg_stride(uint32_t Wp);
 int stage_assignments(gss_ctx* c, const uint8_t* src, uint64_t pitch, uint32_t n, bool device_src);
 // Pack the staged assignment set on stream s.
 int pack_staged(gss_ctx* c, cudaStream_t s);
+// Reserve database capacity for max_clauses clauses and max_lits literals, so that later
+// gss_add_clauses calls within it never move the arrays.
+int reserve_db(gss_ctx* c, uint64_t max_clauses, uint64_t max_lits);
 // Wait for the last test of c and read its record count (status already synchronised when sync = false).
 int wait_test(gss_ctx* c, uint64_t* n, bool sync);
 

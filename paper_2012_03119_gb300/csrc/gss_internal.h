@@ -29,7 +29,7 @@ static_assert(HEAD_K == 16, "kernels read the head as two planes of 8 literals")
 // Device-side status words, reset by the host between phases.
 struct DevStatus {
   unsigned long long n_records;  // records produced by the last test (may exceed capacity)
-  unsigned int bad_code;         // packing saw a value code outside {0, 1, 2}
+  unsigned int bad_code;         // packing saw a value code outside {0, 1, 2}: bit (w mod 32) for plane word w
   unsigned int bad_lit;          // ingest saw a literal >= 2V
   unsigned int bad_size;         // ingest saw an empty clause or offsets beyond the batch
   unsigned int timeout;          // a bounded device wait gave up
@@ -60,6 +60,12 @@ cudaError_t launch_pack(const uint8_t* codes, uint64_t pitch, uint32_t V, uint32
                         const uint32_t* map, uint32_t* P, uint32_t* aggF, uint32_t* aggU, DevStatus* st,
                         cudaStream_t s);
 
+// As launch_pack, but plane word w takes its 32 assignments from code rows
+// word_rows[w] .. word_rows[w] + 31 (device array) of a code array of code_rows rows.
+cudaError_t launch_pack_rows(const uint8_t* codes, uint64_t pitch, uint32_t V, uint32_t N, uint32_t Wp,
+                             uint32_t AWp, const uint32_t* map, const uint32_t* word_rows, uint32_t code_rows,
+                             uint32_t* P, uint32_t* aggF, uint32_t* aggU, DevStatus* st, cudaStream_t s);
+
 // Ingest, in order: validate a batch (offsets -> db offsets at off_db[n0 + 1 ..], literal range);
 // on the first batch rank the variables hot-first (map[v] = internal id; scratch holds
 // rank_scratch_words(V) words); translate the batch literals through map; build head planes.
@@ -72,9 +78,19 @@ cudaError_t launch_translate(uint32_t* lits, uint64_t L, const uint32_t* map, cu
 cudaError_t launch_build_heads(const uint64_t* boff, uint64_t n, uint64_t L0, uint32_t* head0_at_n0,
                                uint32_t* head1_at_n0, const uint32_t* lits_db, uint32_t V, cudaStream_t s);
 
-// Test clauses [c_lo, c_hi) against the planes; append records.
+// Test clauses [c_lo, c_hi) against the planes; append records.  With wm (device, n_wm
+// entries, non-decreasing), clause c is tested against plane word w only if c < wm[w].
 cudaError_t launch_test(int mode, const ClauseView& db, uint64_t c_lo, uint64_t c_hi, const PlaneView& pv,
-                        gss_report* rec, uint64_t cap, DevStatus* st, int grid, cudaStream_t s);
+                        gss_report* rec, uint64_t cap, DevStatus* st, int grid, cudaStream_t s,
+                        const uint64_t* wm = nullptr, uint32_t n_wm = 0);
+
+// Group a serving launch's records by plane word (request) into out: records of word w at
+// [sum of count[0..w), + count[w]), their mask ANDed with nmask[w], records left without a bit
+// dropped, word set to 0.  count / cursor: 32 device counters each (zeroed here); out holds
+// min(st->n_records, cap) records and may be mapped host memory.
+cudaError_t launch_route(const gss_report* rec, const DevStatus* st, uint64_t cap, const uint32_t* nmask, uint32_t k,
+                         unsigned long long* count, unsigned long long* cursor, gss_report* out, int grid,
+                         cudaStream_t s);
 
 // Occupancy-derived persistent grid for launch_test on this device.
 int test_grid_size(int mode, uint32_t AWp, int n_sms);

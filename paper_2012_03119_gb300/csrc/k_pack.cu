@@ -26,6 +26,8 @@
 // stride, so the by-lane write and the coalesced by-word read-out are both
 // bank-conflict free; the read-out derives aggF / aggU with warp ballots.  The
 // producer keeps loading the next variables while consumers write out.
+#include <atomic>
+
 #include <cudaTypedefs.h>
 
 #include "gss_internal.h"
@@ -76,6 +78,7 @@ __device__ __forceinline__ uint32_t stage_of(uint32_t q, uint32_t t, uint32_t w,
 __global__ void __launch_bounds__(PK_THREADS, 2) k_pack(const __grid_constant__ CUtensorMap tmap, uint32_t V,
                                                         uint32_t N, uint32_t Wp, uint32_t AWp,
                                                         const uint32_t* __restrict__ map,
+                                                        const uint32_t* __restrict__ word_rows,
                                                         uint32_t* __restrict__ P, uint32_t* __restrict__ aggF,
                                                         uint32_t* __restrict__ aggU, DevStatus* st) {
   extern __shared__ uint8_t smem_raw[];
@@ -107,7 +110,8 @@ __global__ void __launch_bounds__(PK_THREADS, 2) k_pack(const __grid_constant__ 
           if (uses[s] > 0u) ok = ptx::mbar_wait(&S.empty[s], (uses[s] - 1u) & 1u);  // previous use consumed
           if (!ok || S.err) { ok = false; break; }
           ptx::mbar_expect_tx(&S.full[s], PK_BOX);
-          ptx::tma_load_2d(S.ring[s], &tmap, (int32_t)(t * PK_VT), (int32_t)(w * PK_ROWS), &S.full[s]);
+          const uint32_t row0 = word_rows ? __ldg(word_rows + w) : w * PK_ROWS;  // first code row of word w
+          ptx::tma_load_2d(S.ring[s], &tmap, (int32_t)(t * PK_VT), (int32_t)row0, &S.full[s]);
           ++uses[s];
         }
       }
@@ -165,8 +169,10 @@ __global__ void __launch_bounds__(PK_THREADS, 2) k_pack(const __grid_constant__ 
               else f[r >> 3] |= (x << (sh - 1)) & (0x01010101u << sh);
               tt[r >> 3] |= (x << sh) & (0x01010101u << sh);
             }
-            // invalid codes: a bit above bit 1 of a byte, or code 3 (F and T bits both set)
-            bad |= (any & 0xFCFCFCFCu) | (f[0] & tt[0]) | (f[1] & tt[1]) | (f[2] & tt[2]) | (f[3] & tt[3]);
+            // invalid codes: a bit above bit 1 of a byte, or code 3 (F and T bits both set);
+            // flagged per plane word (mod 32) so that a caller can tell which word held them
+            if ((any & 0xFCFCFCFCu) | (f[0] & tt[0]) | (f[1] & tt[1]) | (f[2] & tt[2]) | (f[3] & tt[3]))
+              bad |= 1u << (w & 31u);
           }
           __syncwarp();
           if (lane == 0) ptx::mbar_arrive(&S.empty[s]);  // the box may be overwritten now
@@ -216,7 +222,7 @@ __global__ void __launch_bounds__(PK_THREADS, 2) k_pack(const __grid_constant__ 
       ptx::named_bar_sync(BAR_CONSUMERS, 32 * PK_CONSUMERS);
     }
   }
-  if (bad) atomicOr(&st->bad_code, 1u);
+  if (bad) atomicOr(&st->bad_code, bad);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -233,9 +239,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 }  // namespace
 
-cudaError_t launch_pack(const uint8_t* codes, uint64_t pitch, uint32_t V, uint32_t N, uint32_t Wp, uint32_t AWp,
-                        const uint32_t* map, uint32_t* P, uint32_t* aggF, uint32_t* aggU, DevStatus* st,
-                        cudaStream_t s) {
+cudaError_t launch_pack_rows(const uint8_t* codes, uint64_t pitch, uint32_t V, uint32_t N, uint32_t Wp,
+                             uint32_t AWp, const uint32_t* map, const uint32_t* word_rows, uint32_t code_rows,
+                             uint32_t* P, uint32_t* aggF, uint32_t* aggU, DevStatus* st, cudaStream_t s) {
   // PAD literal rows 2V, 2V+1: all ones in P and aggF (neutral under AND); aggU row V: zero.
   cudaError_t e = cudaMemsetAsync(P + 2ull * V * Wp, 0xFF, 2ull * Wp * sizeof(uint32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(aggF + 2ull * V * AWp, 0xFF, 2ull * AWp * sizeof(uint32_t), s);
@@ -245,7 +251,7 @@ cudaError_t launch_pack(const uint8_t* codes, uint64_t pitch, uint32_t V, uint32
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap tmap;
-  const cuuint64_t dims[2] = {V, N};
+  const cuuint64_t dims[2] = {V, word_rows ? code_rows : N};
   const cuuint64_t strides[1] = {pitch};
   const cuuint32_t box[2] = {PK_VT, PK_ROWS};
   const cuuint32_t estr[2] = {1, 1};
@@ -256,18 +262,24 @@ cudaError_t launch_pack(const uint8_t* codes, uint64_t pitch, uint32_t V, uint32
   const size_t smem = sizeof(PackSmem) + 128;
   int dev = 0, n_sms = 1;
   cudaGetDevice(&dev);
-  static bool smem_set[64] = {};  // once per device, before any graph capture that packs
-  if (dev < 0 || dev >= 64 || !smem_set[dev]) {
+  static std::atomic<bool> smem_set[64];  // once per device, before any graph capture that packs
+  if (dev < 0 || dev >= 64 || !smem_set[dev].load(std::memory_order_acquire)) {
     e = cudaFuncSetAttribute(k_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64) smem_set[dev] = true;
+    if (dev >= 0 && dev < 64) smem_set[dev].store(true, std::memory_order_release);
   }
   cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev);
   const uint32_t n_vt = (V + PK_VT - 1) / PK_VT;
   const uint32_t slots = 2u * (uint32_t)n_sms;  // two CTAs fit on an SM
   const uint32_t grid = n_vt < slots ? n_vt : slots;
-  k_pack<<<grid, PK_THREADS, smem, s>>>(tmap, V, N, Wp, AWp, map, P, aggF, aggU, st);
+  k_pack<<<grid, PK_THREADS, smem, s>>>(tmap, V, N, Wp, AWp, map, word_rows, P, aggF, aggU, st);
   return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const uint8_t* codes, uint64_t pitch, uint32_t V, uint32_t N, uint32_t Wp, uint32_t AWp,
+                        const uint32_t* map, uint32_t* P, uint32_t* aggF, uint32_t* aggU, DevStatus* st,
+                        cudaStream_t s) {
+  return launch_pack_rows(codes, pitch, V, N, Wp, AWp, map, nullptr, 0, P, aggF, aggU, st, s);
 }
 
 }  // namespace gss

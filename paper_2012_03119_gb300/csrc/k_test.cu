@@ -217,10 +217,33 @@ __device__ __forceinline__ void warp_append(bool has, uint32_t c, uint32_t g, ui
 
 // Stage A and stage B for the tile of clauses [c0, min(c0 + 32, c_hi)), whose head0 is in
 // S.ring[s]; records go to rec / n_records.
+// Live plane words of clause c under per-word watermarks wm[0 .. n_wm) (non-decreasing, in
+// shared memory): word w is tested iff c < wm[w]; without watermarks every word is live.
+template <int AW>
+__device__ __forceinline__ void live_words(const uint64_t* wm, uint32_t n_wm, uint64_t c, uint32_t (&af)[AW]) {
+  if (!wm) {
+#pragma unroll
+    for (int i = 0; i < AW; ++i) af[i] = FULL;
+    return;
+  }
+  uint32_t lo = 0, hi = n_wm;  // k = number of words whose watermark is <= c
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) / 2;
+    if (wm[mid] <= c) lo = mid + 1;
+    else hi = mid;
+  }
+#pragma unroll
+  for (int i = 0; i < AW; ++i) {
+    const uint32_t b = 32u * i;
+    af[i] = lo <= b ? FULL : (lo >= b + 32u ? 0u : (FULL << (lo - b)));
+  }
+}
+
 template <int MODE, int AW>
 __device__ __forceinline__ void test_tile(const ClauseView& db, const PlaneView& pv, const HotRows& hot, WarpSmem& S,
                                           int s, uint64_t c0, uint64_t c_hi, uint32_t lane,
-                                          gss_report* __restrict__ rec, uint64_t cap, unsigned long long* n_records) {
+                                          gss_report* __restrict__ rec, uint64_t cap, unsigned long long* n_records,
+                                          const uint64_t* wm = nullptr, uint32_t n_wm = 0) {
   const uint32_t PAD = db.pad;
   const uint64_t c = c0 + lane;
   const bool act = c < c_hi;
@@ -229,7 +252,8 @@ __device__ __forceinline__ void test_tile(const ClauseView& db, const PlaneView&
   // ---------------- stage A: group (aggregate) test of this lane's clause
   uint32_t af[AW], ou[AW];
 #pragma unroll
-  for (int i = 0; i < AW; ++i) { af[i] = act ? FULL : 0u; ou[i] = 0u; }
+  live_words<AW>(wm, n_wm, c, af);
+  for (int i = 0; i < AW; ++i) { af[i] = act ? af[i] : 0u; ou[i] = 0u; }
   if (act) {
     uint32_t l[8], l1[8];
     const uint4 a = reinterpret_cast<const uint4*>(h0)[0], b = reinterpret_cast<const uint4*>(h0)[1];
@@ -294,8 +318,10 @@ __device__ __forceinline__ void test_tile(const ClauseView& db, const PlaneView&
 
 template <int MODE, int AW>
 __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c_lo, uint64_t c_hi, PlaneView pv,
-                                                       gss_report* __restrict__ rec, uint64_t cap, DevStatus* st) {
+                                                       gss_report* __restrict__ rec, uint64_t cap, DevStatus* st,
+                                                       const uint64_t* __restrict__ wm, uint32_t n_wm) {
   __shared__ WarpSmem smem[TEST_WARPS];
+  __shared__ uint64_t s_wm[32 * AW];  // per-word clause watermarks (serving launches)
   __shared__ __align__(16) uint32_t hotF[HOT_WORDS];
   __shared__ __align__(16) uint32_t hotU[MODE == GSS_MODE_TRIGGER ? HOT_WORDS / 2 : 4];
   if (st->bad_code) return;  // the assignment set held an invalid value code: no records
@@ -307,7 +333,10 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c
   for (uint32_t i = threadIdx.x; i < hot.nU * AW; i += TEST_THREADS) hotU[i] = __ldg(pv.aggU + i);
   hot.F = hotF;
   hot.U = hotU;
+  if (n_wm > 32u * AW) n_wm = 32u * AW;
+  for (uint32_t i = threadIdx.x; wm && i < n_wm; i += TEST_THREADS) s_wm[i] = wm[i];
   __syncthreads();
+  const uint64_t* wms = wm ? s_wm : nullptr;
   const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
   WarpSmem& S = smem[wib];
   const uint64_t warp_id = (uint64_t)blockIdx.x * TEST_WARPS + wib;
@@ -346,7 +375,7 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c
       __syncwarp();
       return;
     }
-    test_tile<MODE, AW>(db, pv, hot, S, s, c_lo + t * 32u, c_hi, lane, rec, cap, &st->n_records);
+    test_tile<MODE, AW>(db, pv, hot, S, s, c_lo + t * 32u, c_hi, lane, rec, cap, &st->n_records, wms, n_wm);
     __syncwarp();
   }
 }
@@ -447,8 +476,8 @@ __global__ void k_batch_reset(const BatchInst* __restrict__ inst, uint32_t n_ins
 
 template <int MODE, int AW>
 void launch_one(const ClauseView& db, uint64_t c_lo, uint64_t c_hi, const PlaneView& pv, gss_report* rec,
-                uint64_t cap, DevStatus* st, int grid, cudaStream_t s) {
-  k_test<MODE, AW><<<grid, TEST_THREADS, 0, s>>>(db, c_lo, c_hi, pv, rec, cap, st);
+                uint64_t cap, DevStatus* st, int grid, cudaStream_t s, const uint64_t* wm, uint32_t n_wm) {
+  k_test<MODE, AW><<<grid, TEST_THREADS, 0, s>>>(db, c_lo, c_hi, pv, rec, cap, st, wm, n_wm);
 }
 
 template <int MODE, int AW>
@@ -508,20 +537,21 @@ int test_batch_grid_size(int mode, uint32_t AWp, int n_sms) {
 }
 
 cudaError_t launch_test(int mode, const ClauseView& db, uint64_t c_lo, uint64_t c_hi, const PlaneView& pv,
-                        gss_report* rec, uint64_t cap, DevStatus* st, int grid, cudaStream_t s) {
+                        gss_report* rec, uint64_t cap, DevStatus* st, int grid, cudaStream_t s, const uint64_t* wm,
+                        uint32_t n_wm) {
   if (c_hi <= c_lo) return cudaSuccess;
   const uint64_t tiles = (c_hi - c_lo + 31) / 32;
   const uint64_t max_blocks = (tiles + TEST_WARPS - 1) / TEST_WARPS;
   if ((uint64_t)grid > max_blocks) grid = (int)max_blocks;
   if (grid < 1) grid = 1;
   if (mode == GSS_MODE_ALLF) {
-    if (pv.AWp == 1) launch_one<GSS_MODE_ALLF, 1>(db, c_lo, c_hi, pv, rec, cap, st, grid, s);
-    else if (pv.AWp == 2) launch_one<GSS_MODE_ALLF, 2>(db, c_lo, c_hi, pv, rec, cap, st, grid, s);
-    else launch_one<GSS_MODE_ALLF, 4>(db, c_lo, c_hi, pv, rec, cap, st, grid, s);
+    if (pv.AWp == 1) launch_one<GSS_MODE_ALLF, 1>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm);
+    else if (pv.AWp == 2) launch_one<GSS_MODE_ALLF, 2>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm);
+    else launch_one<GSS_MODE_ALLF, 4>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm);
   } else {
-    if (pv.AWp == 1) launch_one<GSS_MODE_TRIGGER, 1>(db, c_lo, c_hi, pv, rec, cap, st, grid, s);
-    else if (pv.AWp == 2) launch_one<GSS_MODE_TRIGGER, 2>(db, c_lo, c_hi, pv, rec, cap, st, grid, s);
-    else launch_one<GSS_MODE_TRIGGER, 4>(db, c_lo, c_hi, pv, rec, cap, st, grid, s);
+    if (pv.AWp == 1) launch_one<GSS_MODE_TRIGGER, 1>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm);
+    else if (pv.AWp == 2) launch_one<GSS_MODE_TRIGGER, 2>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm);
+    else launch_one<GSS_MODE_TRIGGER, 4>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm);
   }
   return cudaGetLastError();
 }

@@ -265,3 +265,50 @@ def batch_instance(spec: dict) -> Instance:
     codes = assign_trail(V, N, 0.30, 0.70, s)
     pl = plant(off, lits, codes, spec["n_planted"], s)
     return Instance(f"batch[{spec['index']}]", V, off, lits, codes, pl, params=dict(config=3, **spec))
+
+
+@dataclass
+class ServeWorkload:
+    """A growing clause database and the request snapshots that query it."""
+    n_vars: int
+    offsets: np.ndarray   # uint64 [m_final + 1]: the initial clauses then every batch, in arrival order
+    lits: np.ndarray      # uint32
+    n_initial: int        # clauses resident before the first request
+    batch: int            # clauses per later batch
+    n_batches: int
+    params: dict = field(default_factory=dict)
+
+    def batch_range(self, i: int) -> tuple[int, int]:
+        """Clause ids [lo, hi) of batch i (batch -1 is the initial database)."""
+        if i < 0:
+            return 0, self.n_initial
+        lo = self.n_initial + i * self.batch
+        return lo, lo + self.batch
+
+    def csr(self, lo: int, hi: int) -> tuple[np.ndarray, np.ndarray]:
+        """Clauses [lo, hi) as a CSR of their own (offsets rebased to 0)."""
+        b, e = int(self.offsets[lo]), int(self.offsets[hi])
+        return (self.offsets[lo:hi + 1] - np.uint64(b)).astype(np.uint64), self.lits[b:e]
+
+
+def serve_workload(scale: float = 1.0, seed: int | None = None, n_batches: int = 80) -> ServeWorkload:
+    """Serving workload: 1M vars; 2M clauses resident at the start, then n_batches batches of
+    50k (6M at the end); clause sizes 2 + Geom(1/7) redrawn above 30 (mean 8) as in the tiny
+    workload, Zipf(1.1) vars, fair signs.  ``scale`` shrinks V and every clause count."""
+    s = seed_for(4) if seed is None else seed
+    V = max(64, int(round(1_000_000 * scale)))
+    m0 = max(1, int(round(2_000_000 * scale)))
+    b = max(1, int(round(50_000 * scale)))
+    m = m0 + n_batches * b
+    sizes = clause_sizes(m, "geom", 1.0 / 7.0, 0.0, 30, V, s)
+    off = offsets_from_sizes(sizes)
+    lits = clause_lits(off, V, s)
+    return ServeWorkload(V, off, lits, m0, b, n_batches, dict(
+        config=4, seed=s, scale=scale, sizes="geom(1/7)+2<=30", zipf=1.1, initial=m0, batch=b, n_batches=n_batches))
+
+
+def serve_snapshots(n_vars: int, n: int, seed: int, lo: float = 0.40, hi: float = 0.60) -> np.ndarray:
+    """n request snapshots, uint8 [n, 32, V]: snapshot i is one trail-prefix group of 32
+    assignments (its own variable order and polarity, f ~ U[lo, hi) assigned, the last 2 % of
+    each prefix re-decided), standing in for one solver thread's parent assignments."""
+    return assign_trail(n_vars, 32 * n, lo, hi, seed).reshape(n, 32, n_vars)

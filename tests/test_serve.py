@@ -1,0 +1,218 @@
+"""Serving (gss_server_*): continuous batching of 32-assignment requests against a growing
+resident database.  Every request must equal the oracle on the database prefix given by its
+watermark, and the same request must give the same records alone and in a mix of concurrent
+requests while clauses stream in."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_2012_03119_gb300 as gss
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def work():
+    # 10k vars, 20k clauses at the start, then 20 batches of 500 (30k at the end)
+    return synth.serve_workload(scale=0.01, seed=0x5E17E, n_batches=20)
+
+
+@pytest.fixture(scope="module")
+def snaps(work):
+    return synth.serve_snapshots(work.n_vars, 24, seed=0x5A9)
+
+
+def make_server(work, **kw):
+    args = dict(max_clauses=len(work.offsets) + 1024, max_lits=int(work.offsets[-1]) + 65536, slots=16, lanes=2,
+                lane_report_capacity=1 << 20)
+    args.update(kw)
+    return gss.Server(work.n_vars, **args)
+
+
+def prefix_oracle(work, wm, codes, mode=oracle.MODE_ALLF):
+    off = work.offsets[: wm + 1]
+    return oracle.pairs(off, work.lits[: int(off[-1])], codes, mode)
+
+
+def run_alone(srv, codes, wm=None):
+    rid = srv.submit(codes, watermark=wm, wait_us=10_000_000)
+    rec, info = srv.wait(rid)
+    return gss.expand_reports(rec), info
+
+
+def test_serve_alone_mixed_and_oracle(work, snaps):
+    srv = make_server(work, lanes=2)
+    with srv:
+        srv.add_clauses(*work.csr(0, work.n_initial))
+        probes = [(i, work.n_initial - 3000 * i) for i in range(4)]
+        alone = {}
+        for i, wm in probes:
+            pairs, info = run_alone(srv, snaps[i], wm)
+            assert info["watermark"] == wm and info["batch_words"] == 1
+            np.testing.assert_array_equal(pairs, prefix_oracle(work, wm, snaps[i]))
+            assert len(pairs) > 0
+            alone[i] = pairs
+
+        results, errors = [], []
+        lock = threading.Lock()
+
+        def ingest():
+            try:
+                for b in range(work.n_batches):
+                    srv.add_clauses(*work.csr(*work.batch_range(b)))
+                    time.sleep(0.002)
+            except Exception as e:  # reported by the main thread
+                errors.append(e)
+
+        def client(t):
+            try:
+                ids = []
+                for j in range(5):
+                    k = (t * 5 + j) % len(snaps)
+                    rid = srv.submit(snaps[k], wait_us=10_000_000)
+                    ids.append((k, rid))
+                for k, rid in ids:
+                    rec, info = srv.wait(rid)
+                    with lock:
+                        results.append((k, rec, info))
+            except Exception as e:
+                errors.append(e)
+
+        threads = [threading.Thread(target=ingest)] + [threading.Thread(target=client, args=(t,)) for t in range(8)]
+        for th in threads:
+            th.start()
+        mixed = {}
+        for i, wm in probes:  # the same probes again, inside the mix
+            mixed[i], info = run_alone(srv, snaps[i], wm)
+            assert info["watermark"] == wm
+        for th in threads:
+            th.join()
+        assert not errors, errors
+        st = srv.stats()
+
+    for i, _ in probes:
+        np.testing.assert_array_equal(mixed[i], alone[i])
+    assert len(results) == 40
+    final = len(work.offsets) - 1
+    for k, rec, info in results:
+        wm = info["watermark"]
+        assert work.n_initial <= wm <= final
+        assert (rec["word"] == 0).all()
+        np.testing.assert_array_equal(gss.expand_reports(rec), prefix_oracle(work, wm, snaps[k]))
+    assert st["committed_clauses"] == final
+    assert st["completed"] == st["submitted"] == 48 and st["dropped"] == 0
+    assert st["words_launched"] == 48
+    assert st["launches"] < st["words_launched"], "no launch carried more than one request"
+    assert st["p99_us"] >= st["p50_us"] > 0
+
+
+def test_serve_partial_requests_trigger(work, snaps):
+    """Requests with fewer than 32 assignments: the U rows that pad the plane word must not
+    report, even where a unit clause triggers on an all-U assignment (Definition "triggers")."""
+    off0, lits0 = work.csr(0, work.n_initial)
+    rng = np.random.default_rng(7)
+    units = rng.integers(0, 2 * work.n_vars, size=300).astype(np.uint32)
+    off = np.concatenate([off0, off0[-1] + np.arange(1, len(units) + 1, dtype=np.uint64)])
+    lits = np.concatenate([lits0, units])
+    for mode, ofn in ((gss.GSS_MODE_TRIGGER, oracle.trigger_pairs), (gss.GSS_MODE_ALLF, oracle.allf_pairs)):
+        with make_server(work, mode=mode) as srv:
+            srv.add_clauses(off, lits)
+            for n in (1, 5, 31, 32):
+                codes = np.ascontiguousarray(snaps[n % len(snaps), :n])
+                pairs, info = run_alone(srv, codes)
+                assert info["n_assign"] == n
+                np.testing.assert_array_equal(pairs, ofn(off, lits, codes))
+                if mode == gss.GSS_MODE_TRIGGER:
+                    assert len(pairs) > 0
+
+
+def test_serve_admission_busy(work, snaps):
+    """One slot, four submitters that do not wait: some submissions are refused
+    (GSS_E_BUSY, the request is not sent), every admitted one completes, none is lost."""
+    with make_server(work, slots=1, lanes=1) as srv:
+        assert srv.stats()["slots"] == 1
+        srv.add_clauses(*work.csr(0, work.n_initial))
+        admitted = []
+
+        def client(t):
+            for j in range(30):
+                rid = srv.submit(snaps[(t + j) % len(snaps)], wait_us=0, keep=False)
+                admitted.append(rid is not None)
+
+        threads = [threading.Thread(target=client, args=(t,)) for t in range(4)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+        deadline = time.time() + 30
+        while True:
+            st = srv.stats()
+            if st["completed"] + st["dropped"] == st["submitted"] or time.time() > deadline:
+                break
+            time.sleep(0.01)
+        assert st["submitted"] == 120
+        assert st["dropped"] == admitted.count(False) > 0
+        assert st["completed"] == admitted.count(True) > 0
+        # a submitter that waits for a slot is always admitted
+        pairs, _ = run_alone(srv, snaps[0])
+        np.testing.assert_array_equal(pairs, prefix_oracle(work, work.n_initial, snaps[0]))
+
+
+def test_serve_slot_memory_budget(work):
+    slot = 32 * ((work.n_vars + 15) // 16 * 16)
+    with make_server(work, slots=64, slot_memory_bytes=3 * slot + 17) as srv:
+        assert srv.stats()["slots"] == 3
+    with pytest.raises(gss.GssError) as ei:
+        make_server(work, slot_memory_bytes=slot - 1)
+    assert ei.value.code == gss.GSS_E_NOMEM
+
+
+def test_serve_errors(work, snaps):
+    with make_server(work, max_clauses=1000, max_lits=100_000) as srv:
+        off, lits = work.csr(0, 900)
+        srv.add_clauses(off, lits)
+        with pytest.raises(gss.GssError) as ei:  # past the reserved capacity
+            srv.add_clauses(*work.csr(900, 1200))
+        assert ei.value.code == gss.GSS_E_NOMEM
+        assert srv.stats()["committed_clauses"] == 900
+        with pytest.raises(ValueError):
+            srv.submit(np.zeros((2, work.n_vars + 1), np.uint8))
+        with pytest.raises(gss.GssError) as ei:
+            srv.submit(np.zeros((33, work.n_vars), np.uint8))
+        assert ei.value.code == gss.GSS_E_INVAL
+        # an invalid code spoils its own request only
+        bad = snaps[1].copy()
+        bad[3, 17] = 3
+        rb = srv.submit(bad, wait_us=10_000_000)
+        rg = srv.submit(snaps[2], wait_us=10_000_000)
+        with pytest.raises(gss.GssError) as ei:
+            srv.wait(rb)
+        assert ei.value.code == gss.GSS_E_INVAL
+        rec, info = srv.wait(rg)
+        np.testing.assert_array_equal(gss.expand_reports(rec), prefix_oracle(work, 900, snaps[2]))
+        with pytest.raises(gss.GssError):  # already taken
+            srv.wait(rg)
+        # all-U request: nothing is all-F
+        rec, info = srv.wait(srv.submit(np.zeros((32, work.n_vars), np.uint8), wait_us=10_000_000))
+        assert len(rec) == 0 and info["watermark"] == 900
+
+
+def test_serve_empty_database(work, snaps):
+    with make_server(work) as srv:
+        rec, info = srv.wait(srv.submit(snaps[0], wait_us=10_000_000))
+        assert len(rec) == 0 and info["watermark"] == 0
+        srv.add_clauses(*work.csr(0, 5000))
+        pairs, info = run_alone(srv, snaps[0])
+        assert info["watermark"] == 5000
+        np.testing.assert_array_equal(pairs, prefix_oracle(work, 5000, snaps[0]))
+
+
+def test_serve_identity_layout(work, snaps):
+    with make_server(work, layout=gss.GSS_LAYOUT_IDENTITY) as srv:
+        srv.add_clauses(*work.csr(0, work.n_initial))
+        pairs, _ = run_alone(srv, snaps[3])
+        np.testing.assert_array_equal(pairs, prefix_oracle(work, work.n_initial, snaps[3]))
