@@ -278,7 +278,7 @@ def run_serve(args):
     pool[:] = synth.serve_snapshots(V, n_pool, seed=synth.seed_for(4, 1))
     cap = 1 << 23
     srv = gss.Server(V, max_clauses=final + 1, max_lits=int(w.offsets[-1]) + 1, slots=64, lanes=3,
-                     lane_report_capacity=cap)
+                     lane_report_capacity=cap, tests_in_flight=args.serve_tests_in_flight)
     srv.add_clauses(*w.csr(0, w.n_initial))
     for i in range(max(3, args.warmup)):
         srv.wait(srv.submit(pool[i], wait_us=10_000_000))
@@ -286,7 +286,7 @@ def run_serve(args):
     n_threads, rate = args.serve_threads, args.serve_rate
     period = 0.05
     lock = threading.Lock()
-    done = []  # (watermark, n_assign, records, latency_us, batch_words)
+    done = []  # (watermark, n_assign, records, latency_us, batch_words, admit_us, queue_us, run_us)
     drops = [0]
     errors = []
     t_start = time.perf_counter() + 0.05
@@ -295,7 +295,8 @@ def run_serve(args):
     def keep(r):
         rec, info = r
         with lock:
-            done.append((info["watermark"], info["n_assign"], len(rec), info["latency_us"], info["batch_words"]))
+            done.append((info["watermark"], info["n_assign"], len(rec), info["latency_us"], info["batch_words"],
+                         info["admit_us"], info["queue_us"], info["run_us"]))
 
     def client(t):
         try:
@@ -350,6 +351,7 @@ def run_serve(args):
     if errors:
         raise errors[0]
     lat = np.array([d[3] for d in done])
+    parts = {k: np.array([d[i] for d in done]) for k, i in (("admit", 5), ("queue", 6), ("run", 7))}
     tests_open = sum(d[0] * d[1] for d in done)
 
     # closed loop on the final database: every client keeps one request in flight
@@ -383,20 +385,22 @@ def run_serve(args):
     ctx = gss.Context(V, max_assignments=32, report_capacity=cap)
     ctx.add_clauses(w.offsets, w.lits)
     n_one = min(n_sat, 4 * n_pool)
-    same = True
     for j in range(3):
         ctx.set_assignments(pool[j])
         ctx.test()
         ctx.fetch_reports()
     torch.cuda.synchronize()
+    one_recs = {}
     t0 = time.perf_counter()
     for j in range(n_one):
         ctx.set_assignments(pool[j % n_pool])
         ctx.test()
         rec = ctx.fetch_reports()
         if j in sat_recs:
-            same &= bool(np.array_equal(gss.expand_reports(rec), gss.expand_reports(sat_recs[j])))
+            one_recs[j] = rec
     t_one = time.perf_counter() - t0
+    same = len(one_recs) == len(sat_recs) > 0 and all(
+        np.array_equal(gss.expand_reports(one_recs[j]), gss.expand_reports(sat_recs[j])) for j in sat_recs)
     ctx.close()
     clk = clocks.stop()
 
@@ -406,13 +410,15 @@ def run_serve(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
            "config": {"workload": SERVE_WORKLOAD + (f" (scaled x{args.scale:g})" if args.scale != 1.0 else ""),
                       "threads": n_threads, "rate_req_s": rate, "snapshot_pool": n_pool, "slots": s1["slots"],
-                      "lanes": 3, "final_clauses": final},
+                      "lanes": 3, "tests_in_flight": args.serve_tests_in_flight, "final_clauses": final},
            "open_loop": {"seconds": t_open, "requests": len(done), "dropped": drops[0],
                          "launches": s1["launches"] - s0["launches"],
                          "mean_batch_words": (s1["words_launched"] - s0["words_launched"]) /
                          max(1, s1["launches"] - s0["launches"]),
                          "latency_us": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                                         "max": float(lat.max()), "mean": float(lat.mean())},
+                         "latency_parts_us": {k: {"p50": float(np.percentile(a, 50)), "p99": float(np.percentile(a, 99))}
+                                              for k, a in parts.items()},
                          "records": int(sum(d[2] for d in done)), "req_per_s": len(done) / t_open},
            "saturated": {"requests": n_sat, "seconds": t_sat, "req_per_s": n_sat / t_sat,
                          "G_tests_s": sat_tests / t_sat / 1e9,
@@ -440,6 +446,7 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="requests/s over all simulated solver threads")
     ap.add_argument("--serve-threads", type=int, default=32)
     ap.add_argument("--serve-sat-requests", type=int, default=1024)
+    ap.add_argument("--serve-tests-in-flight", type=int, default=1)
     ap.add_argument("--layout", default="frequency", choices=["frequency", "identity"],
                     help="internal variable numbering of the clause database")
     args = ap.parse_args()

@@ -316,7 +316,12 @@ int gss_test_noalloc(const uint64_t* d_offsets, uint64_t n_clauses, const uint32
  * one of a fixed number of device slots; when none frees up within the caller's wait the
  * submission is refused with GSS_E_BUSY (memory admission).  Admitted requests that are
  * not yet on the GPU join the next launch: a scheduler thread keeps up to `lanes` launches
- * in flight, each testing the clause database against up to 32 requests at once.
+ * in flight, each testing the clause database against up to 32 requests at once.  A new
+ * launch takes every waiting request and starts only while fewer than tests_in_flight
+ * test kernels run: the cost of a launch hardly depends on how many requests it carries
+ * (it streams the whole database prefix once), so under load requests gather into larger
+ * launches instead of splitting the GPU between many small ones; the other lanes overlap
+ * a launch's packing with the routing and copies of the one before.
  *
  * Each request tests the clauses with id < its watermark: the number of clauses committed
  * when it was admitted (or a smaller value the caller asks for).  Its records therefore do
@@ -339,6 +344,8 @@ typedef struct {
   uint32_t lanes;                /* launches in flight at once (1 to 8) */
   uint64_t lane_report_capacity; /* records one launch can hold; more fail the launch's requests */
   uint64_t slot_memory_bytes;    /* non-zero: slots = min(slots, slot_memory_bytes / slot size) */
+  uint32_t tests_in_flight;      /* launches whose test kernels may overlap (default 1; 0: lanes) */
+  uint32_t pad;
 } gss_server_config;
 
 /* Flags of gss_server_submit. */
@@ -351,7 +358,10 @@ typedef struct {
   uint64_t watermark;  /* clauses the request was tested against: ids [0, watermark) */
   uint32_t n_assign;
   uint32_t batch_words; /* requests in the launch that carried it */
-  double latency_us;    /* from the start of gss_server_submit to results on the host */
+  double latency_us;    /* from the start of gss_server_submit to results on the host: */
+  double admit_us;      /*   waiting for a slot and copying the request to the device */
+  double queue_us;      /*   admitted, waiting for a launch */
+  double run_us;        /*   the launch (pack, test, routing) and the hand-over */
 } gss_request_info;
 
 typedef struct {

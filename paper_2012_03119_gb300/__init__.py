@@ -54,12 +54,14 @@ class gss_server_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("mode", ctypes.c_uint32), ("layout", ctypes.c_uint32),
                 ("max_clauses", ctypes.c_uint64), ("max_lits", ctypes.c_uint64), ("slots", ctypes.c_uint32),
                 ("lanes", ctypes.c_uint32), ("lane_report_capacity", ctypes.c_uint64),
-                ("slot_memory_bytes", ctypes.c_uint64)]
+                ("slot_memory_bytes", ctypes.c_uint64), ("tests_in_flight", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32)]
 
 
 class gss_request_info(ctypes.Structure):
     _fields_ = [("watermark", ctypes.c_uint64), ("n_assign", ctypes.c_uint32), ("batch_words", ctypes.c_uint32),
-                ("latency_us", ctypes.c_double)]
+                ("latency_us", ctypes.c_double), ("admit_us", ctypes.c_double), ("queue_us", ctypes.c_double),
+                ("run_us", ctypes.c_double)]
 
 
 class gss_server_stats(ctypes.Structure):
@@ -452,12 +454,13 @@ class Server:
 
     def __init__(self, n_vars: int, device: int = 0, mode: int = GSS_MODE_ALLF, layout: int = GSS_LAYOUT_FREQUENCY,
                  max_clauses: int = 1 << 20, max_lits: int = 1 << 24, slots: int = 64, lanes: int = 3,
-                 lane_report_capacity: int = 1 << 20, slot_memory_bytes: int = 0):
+                 lane_report_capacity: int = 1 << 20, slot_memory_bytes: int = 0, tests_in_flight: int = 1):
         cfg = gss_server_config()
         load().gss_server_config_init(ctypes.byref(cfg))
         cfg.device, cfg.mode, cfg.layout = device, mode, layout
         cfg.max_clauses, cfg.max_lits, cfg.slots, cfg.lanes = max_clauses, max_lits, slots, lanes
         cfg.lane_report_capacity, cfg.slot_memory_bytes = lane_report_capacity, slot_memory_bytes
+        cfg.tests_in_flight = tests_in_flight
         self.n_vars = n_vars
         self.ptr = ctypes.c_void_p()
         rc = load().gss_server_create(ctypes.byref(self.ptr), n_vars, ctypes.byref(cfg))

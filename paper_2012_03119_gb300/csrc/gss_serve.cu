@@ -58,7 +58,7 @@ struct Request {
   uint64_t wm = 0;
   bool keep = false, done = false, overflow = false, bad = false;
   uint32_t batch_words = 0;
-  Clock::time_point t_submit, t_done;
+  Clock::time_point t_submit, t_admit, t_launch, t_done;
   std::vector<gss_report> recs;
 };
 
@@ -86,8 +86,8 @@ struct Lane {
   LaunchOut *d_out = nullptr, *h_out = nullptr;
   cudaEvent_t ev = nullptr;
   std::vector<uint64_t> ids;
-  bool busy = false;
-  std::atomic<int> signalled{0};
+  bool busy = false, testing = false;  // testing: the launch's test kernel may still run
+  std::atomic<int> signalled{0}, tested{0};
 };
 
 }  // namespace
@@ -104,6 +104,7 @@ struct gss_server {
   cudaStream_t copy_stream = nullptr;
   std::vector<Lane> lanes;  // sized once at creation (lanes are not movable)
   int grid = 0, route_grid = 0;
+  uint32_t tests_in_flight = 1;  // launches whose test may overlap
 
   std::mutex mu, ingest_mu;
   std::condition_variable cv_slot, cv_done;
@@ -150,7 +151,13 @@ void wake_scheduler(gss_server* v) {
   v->cv_wake.notify_one();
 }
 
-// Host function at the end of a launch (a driver thread; no CUDA calls here).
+// Host functions after a launch's test and at its end (a driver thread; no CUDA calls here).
+void CUDART_CB lane_tested(void* p) {
+  Lane* L = static_cast<Lane*>(p);
+  L->tested.store(1);
+  wake_scheduler(L->srv);
+}
+
 void CUDART_CB lane_done(void* p) {
   Lane* L = static_cast<Lane*>(p);
   L->signalled.store(1);
@@ -168,6 +175,7 @@ cudaError_t start_launch(gss_server* v, Lane& L) {
   for (uint32_t w = 0; w < k; ++w) {
     Request& r = v->reqs[L.ids[w]];
     r.batch_words = k;
+    r.t_launch = Clock::now();
     L.h_in->rows[w] = r.slot * 32u;
     L.h_in->wm[w] = r.wm;
     L.h_in->nmask[w] = r.n >= 32 ? 0xFFFFFFFFu : ((1u << r.n) - 1u);
@@ -175,8 +183,9 @@ cudaError_t start_launch(gss_server* v, Lane& L) {
   }
   const uint32_t N = 32u * k;
   const uint32_t Wp = words_stride(N), AWp = agg_stride(Wp);
-  L.busy = true;
+  L.busy = L.testing = true;
   L.signalled.store(0);
+  L.tested.store(0);
   v->launches += 1;
   v->words += k;
   cudaError_t e = cudaSuccess;
@@ -191,6 +200,7 @@ cudaError_t start_launch(gss_server* v, Lane& L) {
     const PlaneView pv{L.P, L.aggF, L.aggU, Wp, AWp, N};
     e = launch_test((int)v->mode, v->db, 0, max_wm, pv, L.rec, L.cap, &L.d_out->st, v->grid, L.s, L.d_in->wm, k);
   }
+  if (e == cudaSuccess) e = cudaLaunchHostFunc(L.s, lane_tested, &L);
   if (e == cudaSuccess)
     e = launch_route(L.rec, &L.d_out->st, L.cap, L.d_in->nmask, k, L.d_out->count, L.d_out->cursor, L.h_rec,
                      v->route_grid, L.s);
@@ -224,7 +234,7 @@ void finish_launch(gss_server* v, Lane& L) {
     if (!q.keep) v->reqs.erase(L.ids[w]);
   }
   L.ids.clear();
-  L.busy = false;
+  L.busy = L.testing = false;
   v->cv_slot.notify_all();
   v->cv_done.notify_all();
 }
@@ -239,8 +249,10 @@ void scheduler(gss_server* v) {
       v->wake = false;
     }
     std::lock_guard<std::mutex> g(v->mu);
+    uint32_t testing = 0;
     for (Lane& L : v->lanes) {
       if (!L.busy) continue;
+      if (L.testing && L.tested.exchange(0)) L.testing = false;
       if (L.signalled.exchange(0)) {
         finish_launch(v, L);
         continue;
@@ -252,8 +264,12 @@ void scheduler(gss_server* v) {
         v->stop = true;
       }
     }
+    for (Lane& L : v->lanes) testing += L.testing ? 1u : 0u;
+    // a new launch takes every waiting request; it starts only while fewer than
+    // tests_in_flight tests run, so that requests gather into larger launches under load
     for (Lane& L : v->lanes) {
-      if (v->stop || v->ready.empty() || L.busy) continue;
+      if (v->stop || v->ready.empty() || L.busy || testing >= v->tests_in_flight) continue;
+      ++testing;
       const cudaError_t e = start_launch(v, L);
       if (e != cudaSuccess && v->sched_err == GSS_OK) {
         v->sched_err = GSS_E_CUDA;
@@ -325,6 +341,7 @@ int gss_server_config_init(gss_server_config* c) {
   c->lanes = 3;
   c->lane_report_capacity = 1u << 20;
   c->slot_memory_bytes = 0;
+  c->tests_in_flight = 1;
   return GSS_OK;
 }
 
@@ -403,6 +420,7 @@ int gss_server_create(gss_server** out, uint32_t n_vars, const gss_server_config
   }
   v->grid = test_grid_size((int)cfg.mode, 1, v->ctx->n_sms);
   v->route_grid = 2 * v->ctx->n_sms;
+  v->tests_in_flight = cfg.tests_in_flight ? cfg.tests_in_flight : cfg.lanes;
   v->sched = std::thread(scheduler, v);
   *out = v;
   return GSS_OK;
@@ -473,6 +491,7 @@ int gss_server_submit(gss_server* v, const uint8_t* values, uint32_t n_assign, u
   r.wm = watermark < now_m ? watermark : now_m;
   r.keep = (flags & GSS_SUBMIT_KEEP) != 0;
   r.t_submit = t0;
+  r.t_admit = Clock::now();
   v->ready.push_back(id);
   *request_id = id;
   wake_scheduler(v);
@@ -502,7 +521,11 @@ int gss_server_wait(gss_server* v, uint64_t id, int64_t wait_us, gss_report* out
     info->watermark = rp->wm;
     info->n_assign = rp->n;
     info->batch_words = rp->batch_words;
-    info->latency_us = std::chrono::duration<double, std::micro>(rp->t_done - rp->t_submit).count();
+    auto us = [](Clock::time_point a, Clock::time_point b) { return std::chrono::duration<double, std::micro>(b - a).count(); };
+    info->latency_us = us(rp->t_submit, rp->t_done);
+    info->admit_us = us(rp->t_submit, rp->t_admit);
+    info->queue_us = us(rp->t_admit, rp->t_launch);
+    info->run_us = us(rp->t_launch, rp->t_done);
   }
   if (n > cap && !rp->bad)  // kept: the caller asks again with a larger buffer
     return sfail(v, GSS_E_OVERFLOW, "%llu records > capacity %llu", (unsigned long long)n, (unsigned long long)cap);
