@@ -130,6 +130,21 @@ def make_instance(config: str, rank: int, scale: float):
     raise SystemExit(f"unknown config {config}")
 
 
+def max_over_ranks(x: float, dist=None, device="cuda") -> float:
+    """The largest x over all ranks: a job's time is its slowest rank's."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput in G units/s: every rank processes units_per_rank per step (weak scaling)."""
+    return units_per_rank * world * steps / seconds / 1e9
+
+
 def algorithmic_bytes(inst, n_records: int) -> dict:
     """Bytes the method must move per launch.
     test: 4(m+1) + 4L + 2*V*W*4 + 12*R (offsets, every literal once, each plane row once, records);
@@ -492,6 +507,7 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ctx.add_clauses(inst.offsets, inst.lits)
+    torch.cuda.synchronize()
     ingest_s = time.perf_counter() - t0
 
     d_codes = torch.from_numpy(inst.codes).to(f"cuda:{local}")
@@ -537,10 +553,7 @@ def main():
     elapsed = start.elapsed_time(end) / 1e3
     t_pack = float(np.mean([e[0].elapsed_time(e[1]) for e in ev])) / 1e3
     t_test = float(np.mean([e[1].elapsed_time(e[2]) for e in ev])) / 1e3
-    if dist:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed, dist)
 
     # e2e through the public API from pinned host memory
     e2e_steps = args.e2e_steps or max(3, min(args.steps, 20))
@@ -560,14 +573,10 @@ def main():
         ctx.test()
         ctx.fetch_reports(h_rec)
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist)
     clk = clocks.stop()
 
-    units = m * N * world
-    value = units * args.steps / elapsed / 1e9
+    value = whole_job_rate(m * N, world, args.steps, elapsed)
     pk = peaks()
     B = algorithmic_bytes(inst, n_records)
     roof = {
@@ -590,7 +599,7 @@ def main():
                    "streamed per step)" if args.config == "single" and args.scale == 1.0 else "see sizes",
                    "parallelism": f"weak x{world}: one clause database per GPU, shared assignment set",
                    "layout": args.layout},
-        "e2e": {"value": units * e2e_steps / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": N * V,
+        "e2e": {"value": whole_job_rate(m * N, world, e2e_steps, e2e_s), "unit": UNIT, "h2d_bytes_per_step": N * V,
                 "d2h_bytes_per_step": 12 * n_records + 48},
         "roofline": {k: v for k, v in roof[dominant].items()},
         "roofline_all": roof,
