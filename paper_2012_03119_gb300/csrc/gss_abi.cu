@@ -123,17 +123,22 @@ uint32_t words_stride(uint32_t N) {  // plane row stride in 32-bit words: a powe
 
 uint32_t agg_stride(uint32_t Wp) { return Wp <= 32 ? 1 : Wp / 32; }  // 1, 2 or 4 words
 
-int ensure_planes(gss_ctx* c) {
-  if (c->P) return GSS_OK;
+int ensure_planes(gss_ctx* c) {  // allocates what is missing, so a call after a failed one completes the set
   const uint32_t Wp = words_stride(c->max_N), AWp = agg_stride(Wp);
   int rc;
   void* p;
-  if ((rc = dev_alloc(c, &p, (2ull * c->V + 2) * Wp * 4))) return rc;
-  c->P = static_cast<uint32_t*>(p);
-  if ((rc = dev_alloc(c, &p, (2ull * c->V + 2) * AWp * 4))) return rc;
-  c->aggF = static_cast<uint32_t*>(p);
-  if ((rc = dev_alloc(c, &p, (c->V + 1ull) * AWp * 4))) return rc;
-  c->aggU = static_cast<uint32_t*>(p);
+  if (!c->P) {
+    if ((rc = dev_alloc(c, &p, (2ull * c->V + 2) * Wp * 4))) return rc;
+    c->P = static_cast<uint32_t*>(p);
+  }
+  if (!c->aggF) {
+    if ((rc = dev_alloc(c, &p, (2ull * c->V + 2) * AWp * 4))) return rc;
+    c->aggF = static_cast<uint32_t*>(p);
+  }
+  if (!c->aggU) {
+    if ((rc = dev_alloc(c, &p, (c->V + 1ull) * AWp * 4))) return rc;
+    c->aggU = static_cast<uint32_t*>(p);
+  }
   return GSS_OK;
 }
 

@@ -16,7 +16,7 @@
 // [N][pitch] as 2-D TMA boxes of 32 assignment rows x 128 variables (4 KiB: one
 // plane word of 128 variables) into shared memory; rows past N and variables past V
 // arrive as zeros (U).  Word w of a variable tile belongs to consumer warp w % 8,
-// which owns PK_DEPTH stages of the ring and uses them in its own program order, so
+// which owns D stages of the ring and uses them in its own program order, so
 // each full / empty mbarrier is waited on at most one phase ahead (a parity wait
 // cannot be fooled by a stage two uses behind).  Eight
 // consumer warps transpose boxes: a lane takes 4 codes of each of the 32 rows; the
@@ -39,19 +39,21 @@ namespace {
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int PK_VT = 128;                         // variables per box (bytes per box row)
 constexpr int PK_ROWS = 32;                        // assignment rows per box: one plane word
-constexpr int PK_CONSUMERS = 8;                    // consumer warps
-constexpr int PK_DEPTH = 2;                        // stages owned by each consumer warp
-constexpr int PK_STAGES = PK_CONSUMERS * PK_DEPTH; // ring depth
-constexpr int PK_THREADS = 32 * (PK_CONSUMERS + 1);
-constexpr int PK_BOX = PK_VT * PK_ROWS;            // 8 KiB
+// The shape of a CTA: C consumer warps, each owning D ring stages (the ring holds C * D
+// boxes), MINB CTAs per SM.
+constexpr int PK_CONSUMERS = 8;
+constexpr int PK_DEPTH = 2;
+constexpr int PK_MINB = 2;
+constexpr int PK_BOX = PK_VT * PK_ROWS;            // 4 KiB
 constexpr int PK_STRIDE = 2 * PK_VT + 1;           // staged words per plane word (odd)
 constexpr uint32_t BAR_CONSUMERS = 1;              // named barrier of the consumer warps
 
+template <int C, int D>
 struct PackSmem {
-  uint8_t ring[PK_STAGES][PK_BOX];
+  uint8_t ring[C * D][PK_BOX];
   uint32_t stage[32 * PK_STRIDE];
   uint32_t rowid[PK_VT];  // internal id of each variable of the current tile
-  unsigned long long full[PK_STAGES], empty[PK_STAGES];
+  unsigned long long full[C * D], empty[C * D];
   volatile int err;
 };
 
@@ -62,32 +64,35 @@ __device__ __forceinline__ uint32_t valid_bits(uint32_t N, uint32_t w) {
   return rem >= 32u ? FULL : ((1u << rem) - 1u);
 }
 
-// Sequence number, among the boxes of consumer warp q = w % 8 in this CTA, of word w of
+// Sequence number, among the boxes of consumer warp q = w % C in this CTA, of word w of
 // variable tile t (the CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...).
+template <int C>
 __device__ __forceinline__ uint32_t word_seq(uint32_t q, uint32_t t, uint32_t w, uint32_t Wd, uint32_t b,
                                              uint32_t g) {
-  const uint32_t per_tile = Wd > q ? (Wd - q + PK_CONSUMERS - 1) / PK_CONSUMERS : 0u;  // words of warp q per tile
+  const uint32_t per_tile = Wd > q ? (Wd - q + C - 1) / C : 0u;  // words of warp q per tile
   const uint32_t i = (t - b) / g;                                                      // tiles done before t
-  return i * per_tile + w / PK_CONSUMERS;
+  return i * per_tile + w / C;
 }
+template <int C, int D>
 __device__ __forceinline__ uint32_t stage_of(uint32_t q, uint32_t t, uint32_t w, uint32_t Wd, uint32_t b,
                                              uint32_t g) {
-  return q + PK_CONSUMERS * (word_seq(q, t, w, Wd, b, g) % PK_DEPTH);
+  return q + C * (word_seq<C>(q, t, w, Wd, b, g) % D);
 }
 
-__global__ void __launch_bounds__(PK_THREADS, 2) k_pack(const __grid_constant__ CUtensorMap tmap, uint32_t V,
+template <int C, int D, int MINB>
+__global__ void __launch_bounds__(32 * (C + 1), MINB) k_pack(const __grid_constant__ CUtensorMap tmap, uint32_t V,
                                                         uint32_t N, uint32_t Wp, uint32_t AWp,
                                                         const uint32_t* __restrict__ map,
                                                         const uint32_t* __restrict__ word_rows,
                                                         uint32_t* __restrict__ P, uint32_t* __restrict__ aggF,
                                                         uint32_t* __restrict__ aggU, DevStatus* st) {
   extern __shared__ uint8_t smem_raw[];
-  PackSmem& S = *reinterpret_cast<PackSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  PackSmem<C, D>& S = *reinterpret_cast<PackSmem<C, D>*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   const uint32_t n_vt = (V + PK_VT - 1) / PK_VT;
   const uint32_t Wd = (N + 31) / 32;  // plane words that hold assignments
   if (threadIdx.x == 0) {
-    for (int s = 0; s < PK_STAGES; ++s) {
+    for (int s = 0; s < C * D; ++s) {
       ptx::mbar_init(&S.full[s], 1);
       ptx::mbar_init(&S.empty[s], 1);
     }
@@ -96,17 +101,17 @@ __global__ void __launch_bounds__(PK_THREADS, 2) k_pack(const __grid_constant__ 
   }
   __syncthreads();
 
-  if (warp == PK_CONSUMERS) {  // ---------------- producer
+  if (warp == C) {  // ---------------- producer
     if (lane == 0) {
       ptx::prefetch_tensormap(&tmap);
-      uint32_t uses[PK_STAGES];  // loads issued into each stage so far
-      for (int s = 0; s < PK_STAGES; ++s) uses[s] = 0u;
+      uint32_t uses[C * D];  // loads issued into each stage so far
+      for (int s = 0; s < C * D; ++s) uses[s] = 0u;
       bool ok = true;
       for (uint32_t t = blockIdx.x; t < n_vt && ok; t += gridDim.x) {
         for (uint32_t w = 0; w < Wd; ++w) {
           // word w goes to consumer q = w % 8; its m-th word of this CTA uses stage q + 8 (m % DEPTH)
-          const uint32_t q = w % PK_CONSUMERS;
-          const uint32_t s = stage_of(q, t, w, Wd, blockIdx.x, gridDim.x);
+          const uint32_t q = w % C;
+          const uint32_t s = stage_of<C, D>(q, t, w, Wd, blockIdx.x, gridDim.x);
           if (uses[s] > 0u) ok = ptx::mbar_wait(&S.empty[s], (uses[s] - 1u) & 1u);  // previous use consumed
           if (!ok || S.err) { ok = false; break; }
           ptx::mbar_expect_tx(&S.full[s], PK_BOX);
@@ -120,7 +125,7 @@ __global__ void __launch_bounds__(PK_THREADS, 2) k_pack(const __grid_constant__ 
         atomicOr(&st->timeout, 1u);
       }
       // every issued box must have landed before the CTA may exit (bounded)
-      for (int s = 0; s < PK_STAGES; ++s)
+      for (int s = 0; s < C * D; ++s)
         if (uses[s] > 0u) ptx::mbar_wait(&S.full[s], (uses[s] - 1u) & 1u);
     }
     return;
@@ -145,13 +150,13 @@ __global__ void __launch_bounds__(PK_THREADS, 2) k_pack(const __grid_constant__ 
         const uint32_t v = (t + gridDim.x) * PK_VT + threadIdx.x;
         if (t + gridDim.x < n_vt) next_row = v < V ? (map ? __ldg(map + v) : v) : 0u;
       }
-      for (uint32_t wl = warp; wl < nw; wl += PK_CONSUMERS) {
+      for (uint32_t wl = warp; wl < nw; wl += C) {
         const uint32_t w = wc + wl;
         uint32_t f[4] = {0u, 0u, 0u, 0u}, tt[4] = {0u, 0u, 0u, 0u};
         if (w < Wd) {
-          const uint32_t m = word_seq(warp, t, w, Wd, blockIdx.x, gridDim.x);
-          const uint32_t s = warp + PK_CONSUMERS * (m % PK_DEPTH);
-          bool ok = !S.err && ptx::mbar_wait(&S.full[s], (m / PK_DEPTH) & 1u);
+          const uint32_t m = word_seq<C>(warp, t, w, Wd, blockIdx.x, gridDim.x);
+          const uint32_t s = warp + C * (m % D);
+          bool ok = !S.err && ptx::mbar_wait(&S.full[s], (m / D) & 1u);
           if (!__all_sync(FULL, ok)) {
             if (lane == 0 && !S.err) {
               S.err = 1;
@@ -193,10 +198,10 @@ __global__ void __launch_bounds__(PK_THREADS, 2) k_pack(const __grid_constant__ 
         sw[6 * 32] = __byte_perm(fc, fd, 0x7632);
         sw[7 * 32] = __byte_perm(tc, td, 0x7632);
       }
-      ptx::named_bar_sync(BAR_CONSUMERS, 32 * PK_CONSUMERS);
+      ptx::named_bar_sync(BAR_CONSUMERS, 32 * C);
       // coalesced write-out over (variable, word) pairs, word index fastest
       const uint32_t total = PK_VT * nw;  // a multiple of 32: every lane runs the same trip count
-      for (uint32_t i = threadIdx.x; i < total; i += 32 * PK_CONSUMERS) {
+      for (uint32_t i = threadIdx.x; i < total; i += 32 * C) {
         const uint32_t vl = i >> lg_nw, wl = i & (nw - 1u);
         const uint32_t kv = vl & 3u, ln = vl >> 2;
         const uint32_t Fw = S.stage[wl * PK_STRIDE + (2u * kv) * 32u + ln];
@@ -219,7 +224,7 @@ __global__ void __launch_bounds__(PK_THREADS, 2) k_pack(const __grid_constant__ 
           }
         }
       }
-      ptx::named_bar_sync(BAR_CONSUMERS, 32 * PK_CONSUMERS);
+      ptx::named_bar_sync(BAR_CONSUMERS, 32 * C);
     }
   }
   if (bad) atomicOr(&st->bad_code, bad);
@@ -235,6 +240,28 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
       fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
   }
   return fn;
+}
+
+// Launch k_pack<C, D, MINB> over every variable tile: MINB persistent CTAs per SM.
+template <int C, int D, int MINB>
+cudaError_t launch_pack_cfg(const CUtensorMap& tmap, uint32_t V, uint32_t N, uint32_t Wp, uint32_t AWp,
+                            const uint32_t* map, const uint32_t* word_rows, uint32_t* P, uint32_t* aggF,
+                            uint32_t* aggU, DevStatus* st, cudaStream_t s) {
+  const size_t smem = sizeof(PackSmem<C, D>) + 128;
+  int dev = 0, n_sms = 1;
+  cudaGetDevice(&dev);
+  static std::atomic<bool> smem_set[64];  // once per device, before any graph capture that packs
+  if (dev < 0 || dev >= 64 || !smem_set[dev].load(std::memory_order_acquire)) {
+    const cudaError_t e = cudaFuncSetAttribute(k_pack<C, D, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) smem_set[dev].store(true, std::memory_order_release);
+  }
+  cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint32_t n_vt = (V + PK_VT - 1) / PK_VT;
+  const uint32_t slots = (uint32_t)MINB * (uint32_t)n_sms;
+  const uint32_t grid = n_vt < slots ? n_vt : slots;
+  k_pack<C, D, MINB><<<grid, 32 * (C + 1), smem, s>>>(tmap, V, N, Wp, AWp, map, word_rows, P, aggF, aggU, st);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -259,21 +286,8 @@ cudaError_t launch_pack_rows(const uint8_t* codes, uint64_t pitch, uint32_t V, u
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
-  const size_t smem = sizeof(PackSmem) + 128;
-  int dev = 0, n_sms = 1;
-  cudaGetDevice(&dev);
-  static std::atomic<bool> smem_set[64];  // once per device, before any graph capture that packs
-  if (dev < 0 || dev >= 64 || !smem_set[dev].load(std::memory_order_acquire)) {
-    e = cudaFuncSetAttribute(k_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64) smem_set[dev].store(true, std::memory_order_release);
-  }
-  cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev);
-  const uint32_t n_vt = (V + PK_VT - 1) / PK_VT;
-  const uint32_t slots = 2u * (uint32_t)n_sms;  // two CTAs fit on an SM
-  const uint32_t grid = n_vt < slots ? n_vt : slots;
-  k_pack<<<grid, PK_THREADS, smem, s>>>(tmap, V, N, Wp, AWp, map, word_rows, P, aggF, aggU, st);
-  return cudaGetLastError();
+  return launch_pack_cfg<PK_CONSUMERS, PK_DEPTH, PK_MINB>(tmap, V, N, Wp, AWp, map, word_rows, P, aggF, aggU, st,
+                                                         s);
 }
 
 cudaError_t launch_pack(const uint8_t* codes, uint64_t pitch, uint32_t V, uint32_t N, uint32_t Wp, uint32_t AWp,
