@@ -12,13 +12,13 @@
 //   aggF[l] bit g = (P[l][g] != 0)      -- F is in G(l)
 //   aggU[v] bit g = some assignment of group g leaves v U   -- U is in G(v)
 //
-// Structure: two persistent CTAs per SM.  A producer warp streams the value codes
+// Structure: four persistent CTAs per SM.  A producer warp streams the value codes
 // [N][pitch] as 2-D TMA boxes of 32 assignment rows x 128 variables (4 KiB: one
 // plane word of 128 variables) into shared memory; rows past N and variables past V
-// arrive as zeros (U).  Word w of a variable tile belongs to consumer warp w % 8,
+// arrive as zeros (U).  Word w of a variable tile belongs to consumer warp w % C,
 // which owns D stages of the ring and uses them in its own program order, so
 // each full / empty mbarrier is waited on at most one phase ahead (a parity wait
-// cannot be fooled by a stage two uses behind).  Eight
+// cannot be fooled by a stage two uses behind).  The C
 // consumer warps transpose boxes: a lane takes 4 codes of each of the 32 rows; the
 // F bit (bit 1 of a code byte) and the T bit (bit 0) move to bit r % 8 of their byte
 // with one shift and one fused and-or each, and byte permutes turn four 8-row
@@ -40,10 +40,13 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int PK_VT = 128;                         // variables per box (bytes per box row)
 constexpr int PK_ROWS = 32;                        // assignment rows per box: one plane word
 // The shape of a CTA: C consumer warps, each owning D ring stages (the ring holds C * D
-// boxes), MINB CTAs per SM.
-constexpr int PK_CONSUMERS = 8;
-constexpr int PK_DEPTH = 2;
-constexpr int PK_MINB = 2;
+// boxes), MINB CTAs per SM.  Measured on the 1M-variable x 1024-assignment packing: the
+// write-out after each pass is the costly phase, and small CTAs (4 consumers, one stage
+// each, 4 CTAs per SM: 279 us) overlap it across CTAs better than large ones (8 consumers,
+// 2 stages, 2 CTAs: 366 us; deeper rings with 1 CTA per SM: 430-530 us).
+constexpr int PK_CONSUMERS = 4;
+constexpr int PK_DEPTH = 1;
+constexpr int PK_MINB = 4;
 constexpr int PK_BOX = PK_VT * PK_ROWS;            // 4 KiB
 constexpr int PK_STRIDE = 2 * PK_VT + 1;           // staged words per plane word (odd)
 constexpr uint32_t BAR_CONSUMERS = 1;              // named barrier of the consumer warps
@@ -86,6 +89,8 @@ __global__ void __launch_bounds__(32 * (C + 1), MINB) k_pack(const __grid_consta
                                                         const uint32_t* __restrict__ word_rows,
                                                         uint32_t* __restrict__ P, uint32_t* __restrict__ aggF,
                                                         uint32_t* __restrict__ aggU, DevStatus* st) {
+  // the consumer threads load the row ids of a whole tile: one thread per variable
+  static_assert(32 * C >= PK_VT, "k_pack needs at least PK_VT / 32 consumer warps");
   extern __shared__ uint8_t smem_raw[];
   PackSmem<C, D>& S = *reinterpret_cast<PackSmem<C, D>*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
