@@ -12,7 +12,8 @@
 // Variable numbering.  Section 7 observes that reads of assignment values would be
 // cheaper if the values of variables shared by the clauses tested together were kept
 // in shared memory.  The first batch fixes an internal numbering: variables are ranked
-// by decreasing occurrence count (counts bucketed on a log scale with 8 steps per
+// by decreasing occurrence count in a sample of about 4M of the batch's literals (one
+// 32-literal chunk in every `stride`; counts bucketed on a log scale with 8 steps per
 // octave; ties in variable order), the HOT_VARS top-ranked variables take internal ids
 // 0 .. HOT_VARS - 1 in rank order, the variables they displace take the vacated ids, and
 // every other variable keeps its id (so the packing kernel's writes stay sequential).
@@ -45,13 +46,19 @@ __global__ void k_validate(const uint64_t* __restrict__ boff, uint64_t n, uint64
   if (bad_lit) atomicOr(&st->bad_lit, 1u);
 }
 
-// Occurrence count of every variable; lanes holding the same variable add once per warp.
-__global__ void k_count_vars(const uint32_t* __restrict__ lits, uint64_t L, uint32_t* __restrict__ cnt) {
+// Occurrence count of every variable in the chunks 0, stride, 2 stride, ... of 32
+// consecutive literals; lanes holding the same variable add once per warp.  Sampling
+// bounds the atomics on the hottest counters: under Zipf(1.1) one variable can hold an
+// eighth of all literals.
+constexpr uint64_t COUNT_SAMPLE = 4ull << 20;  // literals counted (about)
+__global__ void k_count_vars(const uint32_t* __restrict__ lits, uint64_t L, uint64_t stride,
+                             uint32_t* __restrict__ cnt) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t base = warp * 32u; base < L; base += n_warps * 32u) {
-    const uint64_t i = base + lane;
+  const uint64_t n_chunks = (L + 31) / 32;
+  for (uint64_t ch = warp * stride; ch < n_chunks; ch += n_warps * stride) {
+    const uint64_t i = ch * 32u + lane;
     const uint32_t v = i < L ? (lits[i] >> 1) : 0xFFFFFFFFu;
     const uint32_t same = __match_any_sync(FULL, v);
     if (v != 0xFFFFFFFFu && lane == (uint32_t)(__ffs(same) - 1)) atomicAdd(&cnt[v], (uint32_t)__popc(same));
@@ -214,7 +221,11 @@ cudaError_t launch_rank_vars(const uint32_t* lits, uint64_t L, uint32_t V, uint3
   uint32_t* hot_ids = base + N_BUCKETS;
   cudaError_t e = cudaMemsetAsync(cnt, 0, (uint64_t)V * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
-  if (L) k_count_vars<<<grid_for(L), 256, 0, s>>>(lits, L, cnt);
+  if (L) {
+    const uint64_t n_chunks = (L + 31) / 32, want = COUNT_SAMPLE / 32;
+    const uint64_t stride = n_chunks > want ? n_chunks / want : 1;
+    k_count_vars<<<grid_for((n_chunks + stride - 1) / stride * 32), 256, 0, s>>>(lits, L, stride, cnt);
+  }
   k_bucket_counts<<<nb, 256, 0, s>>>(cnt, V, blockcnt);
   k_bucket_scan<<<1, N_BUCKETS, 0, s>>>(blockcnt, nb, base);
   k_assign_ranks<<<nb, 32, 0, s>>>(cnt, V, blockcnt, base, rank);

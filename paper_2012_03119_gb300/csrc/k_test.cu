@@ -24,8 +24,10 @@
 //     (clause, group) pairs are compacted into shared memory and each lane runs the exact
 //     word recurrence of one pair, again with a batch's gathers in flight together;
 //   * each non-zero word becomes one record {clause, word, mask} (report(i, mask) of
-//     Listing multiTrigger), appended with a ballot, a population count and one atomicAdd
-//     per warp.  Records past the capacity are counted but not written.
+//     Listing multiTrigger), placed with a ballot and a population count into the warp's
+//     outbox in shared memory; a full outbox reserves its space in the output with one
+//     atomicAdd and is written out as whole words.  Records past the capacity are counted
+//     but not written.
 //
 // The PAD literal 2V is neutral in both modes: its P and aggF rows are all ones and its
 // aggU row is zero, so padded head slots need no branch.
@@ -44,11 +46,13 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int TEST_THREADS = 256;
 constexpr int TEST_WARPS = TEST_THREADS / 32;
 constexpr uint32_t PAIR_CAP = 64;        // candidate pairs staged per warp per round
+constexpr uint32_t OUT_CAP = 64;         // records staged per warp before one reservation
 constexpr uint32_t HOT_WORDS = 2048;     // shared words for the hottest aggF rows (8 KiB)
 
 struct __align__(128) WarpSmem {
   uint32_t ring[2][32 * 8];  // head0 of the current and the next tile
   uint32_t pairs[PAIR_CAP];  // owner lane | group << 5
+  uint32_t out[3 * OUT_CAP]; // staged records {clause, word, mask}
   unsigned long long bar[2];
 };
 
@@ -172,18 +176,13 @@ __device__ __forceinline__ void load8_csr(const uint32_t* __restrict__ lits, uin
   for (int j = 0; j < 8; ++j) l[j] = (k0 + j < e) ? __ldg(lits + k0 + j) : pad;
 }
 
-// Exact recurrence of one (clause, word) pair over all the clause's literals.
+// The exact recurrence of a (clause, word) pair past its first 8 literals (head0, already
+// applied): literals 8..15 from head1, then the CSR, while the word is alive.
 template <int MODE>
-__device__ __forceinline__ uint32_t exact_pair(const ClauseView& db, const PlaneView& pv, uint64_t c,
-                                               const uint32_t* __restrict__ h0 /* shared */, uint32_t g) {
-  const uint32_t valid = valid_bits(pv.N, g);
-  uint32_t af = (MODE == GSS_MODE_ALLF) ? FULL : valid, ou = 0u;
+__device__ __forceinline__ void exact_tail(const ClauseView& db, const PlaneView& pv, uint64_t c, uint32_t g,
+                                           uint32_t valid, uint32_t last_head0, uint32_t& af, uint32_t& ou) {
   uint32_t l[8];
-  const uint4 a = reinterpret_cast<const uint4*>(h0)[0], b = reinterpret_cast<const uint4*>(h0)[1];
-  l[0] = a.x; l[1] = a.y; l[2] = a.z; l[3] = a.w;
-  l[4] = b.x; l[5] = b.y; l[6] = b.z; l[7] = b.w;
-  word_batch8<MODE>(pv, l, g, valid, af, ou);
-  if ((af | ou) != 0u && l[7] != db.pad) {
+  if ((af | ou) != 0u && last_head0 != db.pad) {
     load8_global(db.head1 + c * 8u, l);
     word_batch8<MODE>(pv, l, g, valid, af, ou);
     if ((af | ou) != 0u && l[7] != db.pad) {
@@ -194,29 +193,62 @@ __device__ __forceinline__ uint32_t exact_pair(const ClauseView& db, const Plane
       }
     }
   }
-  return af | ou;
 }
 
-__device__ __forceinline__ void warp_append(bool has, uint32_t c, uint32_t g, uint32_t mask, uint32_t lane,
-                                            gss_report* __restrict__ rec, uint64_t cap, unsigned long long* cnt) {
-  const uint32_t ball = __ballot_sync(FULL, has);
-  if (ball == 0u) return;
-  const int leader = __ffs(ball) - 1;
-  unsigned long long base = 0;
-  if ((int)lane == leader) base = atomicAdd(cnt, (unsigned long long)__popc(ball));
-  base = __shfl_sync(FULL, base, leader);
+// Head0 of a staged pair: its owner lane's 8 literals in the warp's ring (PAD for no pair).
+__device__ __forceinline__ void pair_head(const uint32_t* __restrict__ h0, bool has, uint32_t pad, uint32_t (&l)[8]) {
   if (has) {
-    const unsigned long long idx = base + (unsigned long long)__popc(ball & ((1u << lane) - 1u));
-    if (idx < cap) {
-      gss_report r;
-      r.clause_id = c; r.word = g; r.mask = mask;
-      rec[idx] = r;
-    }
+    const uint4 a = reinterpret_cast<const uint4*>(h0)[0], b = reinterpret_cast<const uint4*>(h0)[1];
+    l[0] = a.x; l[1] = a.y; l[2] = a.z; l[3] = a.w;
+    l[4] = b.x; l[5] = b.y; l[6] = b.z; l[7] = b.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) l[j] = pad;
   }
 }
 
-// Stage A and stage B for the tile of clauses [c0, min(c0 + 32, c_hi)), whose head0 is in
-// S.ring[s]; records go to rec / n_records.
+// Records of a warp are staged in shared memory and reserved in the output with one
+// atomicAdd per OUT_CAP records: a single counter shared by every warp of the grid is the
+// contended resource otherwise.  Records past the capacity are counted but not written.
+struct Outbox {
+  gss_report* rec;
+  uint64_t cap;
+  unsigned long long* cnt;
+  uint32_t n;  // staged records (warp-uniform)
+};
+static_assert(sizeof(gss_report) == 12, "gss_report is three 32-bit words");
+
+template <typename Smem>
+__device__ __forceinline__ void out_flush(Smem& S, Outbox& o, uint32_t lane) {
+  __syncwarp();
+  if (o.n == 0u) return;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(o.cnt, (unsigned long long)o.n);
+  base = __shfl_sync(FULL, base, 0);
+  const uint64_t fit = o.cap > base ? 3ull * (o.cap - base) : 0ull;  // words that fit below the capacity
+  uint32_t* dst = reinterpret_cast<uint32_t*>(o.rec) + 3ull * base;
+  for (uint32_t i = lane; i < 3u * o.n; i += 32u)
+    if (i < fit) dst[i] = S.out[i];
+  o.n = 0u;
+  __syncwarp();
+}
+
+template <typename Smem>
+__device__ __forceinline__ void out_append(Smem& S, Outbox& o, bool has, uint32_t c, uint32_t g, uint32_t mask,
+                                           uint32_t lane) {
+  const uint32_t ball = __ballot_sync(FULL, has);
+  if (ball == 0u) return;
+  const uint32_t k = __popc(ball);
+  if (o.n + k > OUT_CAP) out_flush(S, o, lane);
+  if (has) {
+    const uint32_t j = 3u * (o.n + __popc(ball & ((1u << lane) - 1u)));
+    S.out[j] = c;
+    S.out[j + 1] = g;
+    S.out[j + 2] = mask;
+  }
+  o.n += k;
+}
+
 // Live plane words of clause c under per-word watermarks wm[0 .. n_wm) (non-decreasing, in
 // shared memory): word w is tested iff c < wm[w]; without watermarks every word is live.
 template <int AW>
@@ -239,10 +271,11 @@ __device__ __forceinline__ void live_words(const uint64_t* wm, uint32_t n_wm, ui
   }
 }
 
+// Stage A and stage B for the tile of clauses [c0, min(c0 + 32, c_hi)), whose head0 is in
+// S.ring[s]; records are staged in the warp's outbox.
 template <int MODE, int AW>
 __device__ __forceinline__ void test_tile(const ClauseView& db, const PlaneView& pv, const HotRows& hot, WarpSmem& S,
-                                          int s, uint64_t c0, uint64_t c_hi, uint32_t lane,
-                                          gss_report* __restrict__ rec, uint64_t cap, unsigned long long* n_records,
+                                          int s, uint64_t c0, uint64_t c_hi, uint32_t lane, Outbox& out,
                                           const uint64_t* wm = nullptr, uint32_t n_wm = 0) {
   const uint32_t PAD = db.pad;
   const uint64_t c = c0 + lane;
@@ -302,15 +335,18 @@ __device__ __forceinline__ void test_tile(const ClauseView& db, const PlaneView&
     __syncwarp();
     const uint32_t np = total < PAIR_CAP ? total : PAIR_CAP;
     for (uint32_t p0 = 0; p0 < np; p0 += 32u) {
-      const uint32_t p = p0 + lane;
-      uint32_t res = 0u, g = 0u, owner = 0u;
-      if (p < np) {
-        const uint32_t e = S.pairs[p];
-        owner = e & 31u;
-        g = e >> 5;
-        res = exact_pair<MODE>(db, pv, c0 + owner, &S.ring[s][owner * 8u], g);
-      }
-      warp_append(res != 0u, (uint32_t)(c0 + owner), g, res, lane, rec, cap, n_records);
+      const uint32_t pa = p0 + lane;
+      const bool ha = pa < np;
+      const uint32_t ea = ha ? S.pairs[pa] : 0u;
+      const uint32_t oa = ea & 31u, ga = ea >> 5;
+      uint32_t la[8];
+      pair_head(&S.ring[s][oa * 8u], ha, PAD, la);
+      const uint32_t va = valid_bits(pv.N, ga);
+      uint32_t afa = ha ? ((MODE == GSS_MODE_ALLF) ? FULL : va) : 0u, oua = 0u;
+      word_batch8<MODE>(pv, la, ga, va, afa, oua);
+      exact_tail<MODE>(db, pv, c0 + oa, ga, va, la[7], afa, oua);
+      const uint32_t ra = afa | oua;
+      out_append(S, out, ra != 0u, (uint32_t)(c0 + oa), ga, ra, lane);
     }
     __syncwarp();
   }
@@ -360,6 +396,7 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c
   };
   if (lane == 0) issue(warp_id, 0);
 
+  Outbox out{rec, cap, &st->n_records, 0u};
   uint32_t it = 0;
   for (uint64_t t = warp_id; t < n_tiles; t += n_warps, ++it) {
     const int s = it & 1;
@@ -372,12 +409,13 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c
         ptx::mbar_wait(&S.bar[s], (it >> 1) & 1u);
         if (has_next) ptx::mbar_wait(&S.bar[s ^ 1], ((it + 1) >> 1) & 1u);
       }
-      __syncwarp();
+      out_flush(S, out, lane);
       return;
     }
-    test_tile<MODE, AW>(db, pv, hot, S, s, c_lo + t * 32u, c_hi, lane, rec, cap, &st->n_records, wms, n_wm);
+    test_tile<MODE, AW>(db, pv, hot, S, s, c_lo + t * 32u, c_hi, lane, out, wms, n_wm);
     __syncwarp();
   }
+  out_flush(S, out, lane);
 }
 
 // Last instance whose first tile is <= t (instances without clauses are skipped because a
@@ -428,6 +466,8 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test_batch(const BatchInst* __
   };
   uint64_t t = cb;
   if (lane == 0) issue(t, 0);
+  Outbox out{nullptr, 0, nullptr, 0u};
+  uint32_t cur = 0xFFFFFFFFu;  // instance whose records the outbox holds
   for (uint32_t it = 0;; ++it) {
     uint64_t tn = t + 1;
     if (tn >= ce) {  // take the next chunk of tiles
@@ -446,20 +486,25 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test_batch(const BatchInst* __
         ptx::mbar_wait(&S.bar[s], (it >> 1) & 1u);
         if (has_next) ptx::mbar_wait(&S.bar[s ^ 1], ((it + 1) >> 1) & 1u);
       }
-      __syncwarp();
+      out_flush(S, out, lane);
       return;
     }
     const uint32_t i = find_inst(inst, n_inst, t);
     const ClauseView db = inst[i].db;
     const PlaneView pv = inst[i].pv;
     DevStatus* st = inst[i].st;
+    if (i != cur) {  // records go to another instance from here on
+      out_flush(S, out, lane);
+      out = Outbox{inst[i].rec, inst[i].cap, &st->n_records, 0u};
+      cur = i;
+    }
     if (!st->bad_code)
-      test_tile<MODE, AW>(db, pv, hot, S, s, (t - inst[i].tile0) * 32u, inst[i].m, lane, inst[i].rec, inst[i].cap,
-                          &st->n_records);
+      test_tile<MODE, AW>(db, pv, hot, S, s, (t - inst[i].tile0) * 32u, inst[i].m, lane, out);
     __syncwarp();  // every lane is done with ring[s] before it is refilled
     if (!has_next) break;
     t = tn;
   }
+  out_flush(S, out, lane);
 }
 
 // Zero the work counter, the batch status and every instance's test status (records, bad
