@@ -56,6 +56,7 @@ struct PackSmem {
   uint8_t ring[C * D][PK_BOX];
   uint32_t stage[32 * PK_STRIDE];
   uint32_t rowid[PK_VT];  // internal id of each variable of the current tile
+  uint32_t aggw[3 * PK_VT];  // aggregate bits of the pass: aggF rows (2 vl, 2 vl + 1), then aggU (vl)
   unsigned long long full[C * D], empty[C * D];
   volatile int err;
 };
@@ -104,6 +105,7 @@ __global__ void __launch_bounds__(32 * (C + 1), MINB) k_pack(const __grid_consta
     S.err = 0;
     ptx::fence_mbar_init();
   }
+  for (uint32_t i = threadIdx.x; i < 3u * PK_VT; i += blockDim.x) S.aggw[i] = 0u;
   __syncthreads();
 
   if (warp == C) {  // ---------------- producer
@@ -155,6 +157,8 @@ __global__ void __launch_bounds__(32 * (C + 1), MINB) k_pack(const __grid_consta
         const uint32_t v = (t + gridDim.x) * PK_VT + threadIdx.x;
         if (t + gridDim.x < n_vt) next_row = v < V ? (map ? __ldg(map + v) : v) : 0u;
       }
+      // aggregate bits of this lane's 4 variables over the pass's words it transposes
+      uint32_t aF[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u}, aU[4] = {0u, 0u, 0u, 0u};
       for (uint32_t wl = warp; wl < nw; wl += C) {
         const uint32_t w = wc + wl;
         uint32_t f[4] = {0u, 0u, 0u, 0u}, tt[4] = {0u, 0u, 0u, 0u};
@@ -192,16 +196,32 @@ __global__ void __launch_bounds__(32 * (C + 1), MINB) k_pack(const __grid_consta
         const uint32_t fc = __byte_perm(f[0], f[1], 0x7362), fd = __byte_perm(f[2], f[3], 0x7362);
         const uint32_t ta = __byte_perm(tt[0], tt[1], 0x5140), tb = __byte_perm(tt[2], tt[3], 0x5140);
         const uint32_t tc = __byte_perm(tt[0], tt[1], 0x7362), td = __byte_perm(tt[2], tt[3], 0x7362);
-        // staged index of (variable 4 lane + k, literal sign s) = (2 k + s) * 32 + lane
+        // word (variable 4 lane + k, literal sign s) sits at index 2 k + s; staged at (2 k + s) * 32 + lane
+        uint32_t x[8];
+        x[0] = __byte_perm(fa, fb, 0x5410);
+        x[1] = __byte_perm(ta, tb, 0x5410);
+        x[2] = __byte_perm(fa, fb, 0x7632);
+        x[3] = __byte_perm(ta, tb, 0x7632);
+        x[4] = __byte_perm(fc, fd, 0x5410);
+        x[5] = __byte_perm(tc, td, 0x5410);
+        x[6] = __byte_perm(fc, fd, 0x7632);
+        x[7] = __byte_perm(tc, td, 0x7632);
         uint32_t* sw = S.stage + wl * PK_STRIDE + lane;
-        sw[0 * 32] = __byte_perm(fa, fb, 0x5410);
-        sw[1 * 32] = __byte_perm(ta, tb, 0x5410);
-        sw[2 * 32] = __byte_perm(fa, fb, 0x7632);
-        sw[3 * 32] = __byte_perm(ta, tb, 0x7632);
-        sw[4 * 32] = __byte_perm(fc, fd, 0x5410);
-        sw[5 * 32] = __byte_perm(tc, td, 0x5410);
-        sw[6 * 32] = __byte_perm(fc, fd, 0x7632);
-        sw[7 * 32] = __byte_perm(tc, td, 0x7632);
+        const uint32_t bit = 1u << wl, vw = valid_bits(N, w);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          sw[j * 32] = x[j];
+          aF[j] |= x[j] != 0u ? bit : 0u;  // F is in G(l)
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) aU[k] |= (~(x[2 * k] | x[2 * k + 1]) & vw) != 0u ? bit : 0u;  // U is in G(v)
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {  // merge the consumers' bits
+        const uint32_t vl = 4u * lane + (uint32_t)k;
+        if (aF[2 * k]) atomicOr(&S.aggw[2u * vl], aF[2 * k]);
+        if (aF[2 * k + 1]) atomicOr(&S.aggw[2u * vl + 1u], aF[2 * k + 1]);
+        if (aU[k]) atomicOr(&S.aggw[2u * PK_VT + vl], aU[k]);
       }
       ptx::named_bar_sync(BAR_CONSUMERS, 32 * C);
       // coalesced write-out over (variable, word) pairs, word index fastest
@@ -212,21 +232,24 @@ __global__ void __launch_bounds__(32 * (C + 1), MINB) k_pack(const __grid_consta
         const uint32_t Fw = S.stage[wl * PK_STRIDE + (2u * kv) * 32u + ln];
         const uint32_t Tw = S.stage[wl * PK_STRIDE + (2u * kv + 1u) * 32u + ln];
         const uint32_t w = wc + wl;
-        const uint32_t Uw = ~(Fw | Tw) & valid_bits(N, w);
-        const uint32_t bF = __ballot_sync(FULL, Fw != 0u);
-        const uint32_t bT = __ballot_sync(FULL, Tw != 0u);
-        const uint32_t bU = __ballot_sync(FULL, Uw != 0u);
         if (vl < nv) {
           const uint64_t v = S.rowid[vl];  // internal row of variable v0 + vl
           P[(2u * v) * Wp + w] = Fw;
           P[(2u * v + 1u) * Wp + w] = Tw;
-          if (wl == 0u) {  // this variable's nw words sit in lanes [lane, lane + nw); one aggregate word per pass
-            const uint32_t m = nw == 32u ? FULL : ((1u << nw) - 1u);
-            const uint32_t u = wc >> 5;
-            aggF[(2u * v) * AWp + u] = (bF >> lane) & m;
-            aggF[(2u * v + 1u) * AWp + u] = (bT >> lane) & m;
-            aggU[v * AWp + u] = (bU >> lane) & m;
-          }
+        }
+      }
+      if (threadIdx.x < PK_VT) {  // one aggregate word per row and pass; cleared for the next pass
+        const uint32_t vl = threadIdx.x;
+        const uint32_t gF = S.aggw[2u * vl], gT = S.aggw[2u * vl + 1u], gU = S.aggw[2u * PK_VT + vl];
+        S.aggw[2u * vl] = 0u;
+        S.aggw[2u * vl + 1u] = 0u;
+        S.aggw[2u * PK_VT + vl] = 0u;
+        if (vl < nv) {
+          const uint64_t v = S.rowid[vl];
+          const uint32_t u = wc >> 5;
+          aggF[(2u * v) * AWp + u] = gF;
+          aggF[(2u * v + 1u) * AWp + u] = gT;
+          aggU[v * AWp + u] = gU;
         }
       }
       ptx::named_bar_sync(BAR_CONSUMERS, 32 * C);
