@@ -106,6 +106,11 @@ __global__ void __launch_bounds__(32 * (C + 1), MINB) k_pack(const __grid_consta
     ptx::fence_mbar_init();
   }
   for (uint32_t i = threadIdx.x; i < 3u * PK_VT; i += blockDim.x) S.aggw[i] = 0u;
+  if (blockIdx.x == 0) {  // PAD literal rows 2V, 2V + 1: all ones in P and aggF (neutral under AND); aggU row V: zero
+    for (uint32_t i = threadIdx.x; i < 2u * Wp; i += blockDim.x) P[2ull * V * Wp + i] = FULL;
+    for (uint32_t i = threadIdx.x; i < 2u * AWp; i += blockDim.x) aggF[2ull * V * AWp + i] = FULL;
+    for (uint32_t i = threadIdx.x; i < AWp; i += blockDim.x) aggU[(uint64_t)V * AWp + i] = 0u;
+  }
   __syncthreads();
 
   if (warp == C) {  // ---------------- producer
@@ -297,11 +302,12 @@ cudaError_t launch_pack_cfg(const CUtensorMap& tmap, uint32_t V, uint32_t N, uin
 cudaError_t launch_pack_rows(const uint8_t* codes, uint64_t pitch, uint32_t V, uint32_t N, uint32_t Wp,
                              uint32_t AWp, const uint32_t* map, const uint32_t* word_rows, uint32_t code_rows,
                              uint32_t* P, uint32_t* aggF, uint32_t* aggU, DevStatus* st, cudaStream_t s) {
-  // PAD literal rows 2V, 2V+1: all ones in P and aggF (neutral under AND); aggU row V: zero.
-  cudaError_t e = cudaMemsetAsync(P + 2ull * V * Wp, 0xFF, 2ull * Wp * sizeof(uint32_t), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(aggF + 2ull * V * AWp, 0xFF, 2ull * AWp * sizeof(uint32_t), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(aggU + (uint64_t)V * AWp, 0, AWp * sizeof(uint32_t), s);
-  if (e != cudaSuccess || V == 0 || N == 0) return e;
+  if (V == 0 || N == 0) {  // no kernel: the PAD literal rows still have to be set (the kernel writes them otherwise)
+    cudaError_t e = cudaMemsetAsync(P + 2ull * V * Wp, 0xFF, 2ull * Wp * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(aggF + 2ull * V * AWp, 0xFF, 2ull * AWp * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(aggU + (uint64_t)V * AWp, 0, AWp * sizeof(uint32_t), s);
+    return e;
+  }
   if (pitch % 16 != 0 || reinterpret_cast<uintptr_t>(codes) % 16 != 0) return cudaErrorInvalidValue;
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
