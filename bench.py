@@ -525,6 +525,10 @@ def main():
     key = set((pairs[:, 0].astype(np.int64) << 32 | pairs[:, 1]).tolist())
     planted_ok = all(((int(c) << 32) | int(a)) in key for c, a in inst.planted.tolist())
     n_records = len(rec)
+    st = gss.gss_get_stats(ctx.ptr)  # the aggregate test's selectivity (Section 4.2) on this workload
+    aggregate = {"candidate_pairs": st["candidate_pairs"], "group_pairs": st["group_pairs"],
+                 "negative_ratio": 1.0 - st["candidate_pairs"] / max(1, st["group_pairs"]),
+                 "paper_negative_ratio": 0.999422}
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -609,6 +613,7 @@ def main():
                    "GB_per_s": (8 * (m + 1) + 4 * inst.n_lits) / ingest_s / 1e9},
         "gpu_launches": 2 * args.steps,
         "records": n_records, "pairs": int(len(pairs)), "planted_found": planted_ok,
+        "aggregate_test": aggregate,
         "clocks": clk,
     }
     ctx.close()

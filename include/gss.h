@@ -100,6 +100,9 @@ typedef struct {
   uint64_t report_capacity;
   uint64_t tests_run;       /* gss_test calls completed */
   uint64_t pair_tests;      /* sum over gss_test calls of n_clauses * N */
+  uint64_t candidate_pairs; /* last test: (clause, 32-assignment group) pairs whose aggregate test
+                               (Section 4.2) was positive; valid after gss_report_count / fetch */
+  uint64_t group_pairs;     /* last test: n_clauses * ceil(N / 32), all (clause, group) pairs */
 } gss_stats;
 
 /* ------------------------------------------------------------ lifecycle */

@@ -41,7 +41,8 @@ class gss_config(ctypes.Structure):
 class gss_stats(ctypes.Structure):
     _fields_ = [("n_vars", ctypes.c_uint32), ("n_assign", ctypes.c_uint32), ("n_clauses", ctypes.c_uint64),
                 ("n_lits", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64), ("report_capacity", ctypes.c_uint64),
-                ("tests_run", ctypes.c_uint64), ("pair_tests", ctypes.c_uint64)]
+                ("tests_run", ctypes.c_uint64), ("pair_tests", ctypes.c_uint64),
+                ("candidate_pairs", ctypes.c_uint64), ("group_pairs", ctypes.c_uint64)]
 
 
 class gss_batch_info(ctypes.Structure):

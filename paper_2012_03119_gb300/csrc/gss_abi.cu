@@ -390,7 +390,7 @@ int gss_test(gss_ctx* c) {
   c->err.clear();
   if (!c->have_assign) return fail(c, GSS_E_STATE, "gss_test before gss_set_assignments");
   DeviceGuard dg(c->device);
-  CK(c, cudaMemsetAsync(&c->st->n_records, 0, sizeof(unsigned long long), c->stream));
+  CK(c, cudaMemsetAsync(&c->st->n_records, 0, 2 * sizeof(unsigned long long), c->stream));  // records, candidates
   if (c->m && c->N) {
     ClauseView db{c->off, c->lits, c->head0, c->head1, 2u * c->V};
     PlaneView pv{c->P, c->aggF, c->aggU, c->Wp, c->AWp, c->N};
@@ -502,6 +502,8 @@ int gss_get_stats(const gss_ctx* c, gss_stats* o) {
   o->report_capacity = c->rec_cap;
   o->tests_run = c->tests_run;
   o->pair_tests = c->pair_tests;
+  o->candidate_pairs = c->tested ? c->h_st[0].n_candidates : 0;
+  o->group_pairs = c->tested ? c->m * (uint64_t)((c->N + 31) / 32) : 0;
   return GSS_OK;
 }
 

@@ -214,7 +214,9 @@ struct Outbox {
   gss_report* rec;
   uint64_t cap;
   unsigned long long* cnt;
-  uint32_t n;  // staged records (warp-uniform)
+  unsigned long long* cand_cnt;  // candidate-pair counter of the same test
+  uint32_t n;                    // staged records (warp-uniform)
+  uint32_t cand;                 // candidate pairs counted by this lane, not yet added
 };
 static_assert(sizeof(gss_report) == 12, "gss_report is three 32-bit words");
 
@@ -231,6 +233,15 @@ __device__ __forceinline__ void out_flush(Smem& S, Outbox& o, uint32_t lane) {
     if (i < fit) dst[i] = S.out[i];
   o.n = 0u;
   __syncwarp();
+}
+
+// Flush and add the warp's candidate count: at the end, or before the outbox changes target.
+template <typename Smem>
+__device__ __forceinline__ void out_close(Smem& S, Outbox& o, uint32_t lane) {
+  out_flush(S, o, lane);
+  const uint32_t c = __reduce_add_sync(FULL, o.cand);
+  if (lane == 0 && c) atomicAdd(o.cand_cnt, (unsigned long long)c);
+  o.cand = 0u;
 }
 
 template <typename Smem>
@@ -308,7 +319,10 @@ __device__ __forceinline__ void test_tile(const ClauseView& db, const PlaneView&
   }
   uint32_t cand[AW];
 #pragma unroll
-  for (int i = 0; i < AW; ++i) cand[i] = af[i] | ou[i];
+  for (int i = 0; i < AW; ++i) {
+    cand[i] = af[i] | ou[i];
+    out.cand += __popc(cand[i]);  // pairs the aggregate test let through
+  }
 
   // ---------------- stage B: exact test of the warp's candidate (clause, group) pairs
   for (;;) {
@@ -396,7 +410,7 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c
   };
   if (lane == 0) issue(warp_id, 0);
 
-  Outbox out{rec, cap, &st->n_records, 0u};
+  Outbox out{rec, cap, &st->n_records, &st->n_candidates, 0u, 0u};
   uint32_t it = 0;
   for (uint64_t t = warp_id; t < n_tiles; t += n_warps, ++it) {
     const int s = it & 1;
@@ -409,13 +423,13 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c
         ptx::mbar_wait(&S.bar[s], (it >> 1) & 1u);
         if (has_next) ptx::mbar_wait(&S.bar[s ^ 1], ((it + 1) >> 1) & 1u);
       }
-      out_flush(S, out, lane);
+      out_close(S, out, lane);
       return;
     }
     test_tile<MODE, AW>(db, pv, hot, S, s, c_lo + t * 32u, c_hi, lane, out, wms, n_wm);
     __syncwarp();
   }
-  out_flush(S, out, lane);
+  out_close(S, out, lane);
 }
 
 // Last instance whose first tile is <= t (instances without clauses are skipped because a
@@ -466,7 +480,7 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test_batch(const BatchInst* __
   };
   uint64_t t = cb;
   if (lane == 0) issue(t, 0);
-  Outbox out{nullptr, 0, nullptr, 0u};
+  Outbox out{nullptr, 0, nullptr, nullptr, 0u, 0u};
   uint32_t cur = 0xFFFFFFFFu;  // instance whose records the outbox holds
   for (uint32_t it = 0;; ++it) {
     uint64_t tn = t + 1;
@@ -486,7 +500,7 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test_batch(const BatchInst* __
         ptx::mbar_wait(&S.bar[s], (it >> 1) & 1u);
         if (has_next) ptx::mbar_wait(&S.bar[s ^ 1], ((it + 1) >> 1) & 1u);
       }
-      out_flush(S, out, lane);
+      out_close(S, out, lane);
       return;
     }
     const uint32_t i = find_inst(inst, n_inst, t);
@@ -494,8 +508,8 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test_batch(const BatchInst* __
     const PlaneView pv = inst[i].pv;
     DevStatus* st = inst[i].st;
     if (i != cur) {  // records go to another instance from here on
-      out_flush(S, out, lane);
-      out = Outbox{inst[i].rec, inst[i].cap, &st->n_records, 0u};
+      out_close(S, out, lane);
+      out = Outbox{inst[i].rec, inst[i].cap, &st->n_records, &st->n_candidates, 0u, 0u};
       cur = i;
     }
     if (!st->bad_code)
@@ -504,7 +518,7 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test_batch(const BatchInst* __
     if (!has_next) break;
     t = tn;
   }
-  out_flush(S, out, lane);
+  out_close(S, out, lane);
 }
 
 // Zero the work counter, the batch status and every instance's test status (records, bad

@@ -256,3 +256,20 @@ def test_layouts_agree(mode):
             out.append(gss.expand_reports(ctx.run(inst.codes)))
     assert np.array_equal(out[0], out[1])
     assert np.array_equal(out[0], oracle.pairs(inst.offsets, inst.lits, inst.codes, mode))
+
+
+@pytest.mark.parametrize("mode", [ALLF, TRIG])
+@pytest.mark.parametrize("layout", [gss.GSS_LAYOUT_IDENTITY, gss.GSS_LAYOUT_FREQUENCY])
+def test_aggregate_candidates_match_oracle(mode, layout):
+    """Stage A is the aggregate test of Section 4.2 (Listing aggregateTrigger, all-F or
+    trigger): the number of (clause, group) pairs it lets through equals the oracle's count of
+    pairs whose aggregate test is positive, including a ragged last group."""
+    inst = small_instance(n_vars=400, n_clauses=2500, n_assign=80, seed=5)
+    with gss.Context(inst.n_vars, mode=mode, layout=layout, report_capacity=1 << 20, max_assignments=80) as ctx:
+        ctx.add_clauses(inst.offsets, inst.lits)
+        ctx.run(inst.codes)
+        st = gss.gss_get_stats(ctx.ptr)
+    want = oracle.aggregate_pairs(inst.offsets, inst.lits, inst.codes, mode=mode)
+    assert st["group_pairs"] == inst.n_clauses * 3
+    assert st["candidate_pairs"] == len(want)
+    assert 0 < len(want) < st["group_pairs"]
