@@ -66,3 +66,98 @@ def test_pins_reject_mutant(mutant, tiny_instance):
     if mutant != 6:
         fails += pin_invariants(tiny_instance, mutant=mutant)
     assert fails, f"mutant {mutant} ({MUTANTS[mutant]}) passed every pin"
+
+
+# ---------------------------------------------------------------- clause activity (Section 3.6)
+from oracle.activity import ActivityOracle  # noqa: E402
+
+
+def _csr(sizes, n_vars, seed):
+    off = synth.offsets_from_sizes(np.asarray(sizes, np.uint32))
+    return off, synth.clause_lits(off, n_vars, seed)
+
+
+def test_activity_without_decay_counts_reports():
+    """decay = 1: every clause ends at 1 + (number of tests that reported it), exactly."""
+    rng = np.random.default_rng(1)
+    a = ActivityOracle(1.0)
+    a.add(*_csr(rng.integers(1, 6, 50), 40, 1))
+    counts = np.zeros(50, np.int64)
+    for _ in range(30):
+        rep = rng.choice(50, size=rng.integers(0, 20), replace=True)  # repeats: one bump per test
+        counts[np.unique(rep)] += 1
+        a.after_test(rep.astype(np.uint32))
+    assert np.array_equal(a.act, (1 + counts).astype(np.float32))
+
+
+def test_activity_decay_half_is_a_sum_of_powers_of_two():
+    """decay = 1/2 doubles inc after each test: a clause added before test 0 and reported in
+    tests S holds 1 + sum of 2^t over t in S, and a later report outweighs all earlier ones."""
+    rng = np.random.default_rng(2)
+    a = ActivityOracle(0.5)
+    a.add(*_csr(rng.integers(1, 6, 40), 30, 2))
+    want = [1] * 40
+    for t in range(20):
+        rep = np.nonzero(rng.random(40) < 0.3)[0]
+        for c in rep:
+            want[c] += 2 ** t
+        a.after_test(rep.astype(np.uint32))
+    assert [int(x) for x in a.act] == want
+    assert a.inc == np.float32(2.0 ** 20)
+
+
+def test_activity_rescale_keeps_the_order():
+    """70 tests at decay 1/2 push inc past 1e20: activities and inc are scaled by 1e-20 and the
+    ranking of clauses equals the ranking of the exact integer sums."""
+    rng = np.random.default_rng(3)
+    a = ActivityOracle(0.5)
+    a.add(*_csr(rng.integers(1, 6, 60), 50, 3))
+    exact = [1] * 60
+    scaled = False
+    for t in range(70):
+        rep = np.nonzero(rng.random(60) < 0.2)[0]
+        for c in rep:
+            exact[c] += 2 ** t
+        before = a.inc
+        a.after_test(rep.astype(np.uint32))
+        scaled |= a.inc < before
+    assert scaled and a.inc <= np.float32(1e20)
+    order_f = sorted(range(60), key=lambda c: (float(a.act[c]), c))
+    order_x = sorted(range(60), key=lambda c: (exact[c], c))
+    # equal exact sums stay equal; float rounding never swaps two clauses whose sums differ by more than a factor 2^-20
+    for i, j in zip(order_f, order_x):
+        assert i == j or exact[i] == exact[j] or abs(exact[i] - exact[j]) < max(exact[i], exact[j]) >> 20
+
+
+def test_reduce_matches_brute_force_and_keeps_short_clauses():
+    rng = np.random.default_rng(4)
+    a = ActivityOracle(0.9)
+    sizes = rng.integers(1, 9, 300)
+    a.add(*_csr(sizes, 100, 4))
+    for _ in range(12):
+        a.after_test(np.nonzero(rng.random(300) < 0.25)[0].astype(np.uint32))
+    act_before, ids_before = a.act.copy(), a.ids.copy()
+    long_ids = [int(i) for i, s in zip(ids_before, sizes) if s > 2]
+    n_remove = int(0.4 * len(long_ids))
+    gone = set(sorted(long_ids, key=lambda i: (float(act_before[i]), i))[:n_remove])  # brute force
+    assert a.reduce(0.4) == n_remove
+    assert set(a.ids.tolist()) == set(range(300)) - gone
+    assert all(i in set(a.ids.tolist()) for i, s in zip(ids_before, sizes) if s <= 2)
+    assert np.all(np.diff(a.ids.astype(np.int64)) > 0)
+    assert np.array_equal(np.diff(a.offsets), sizes[a.ids])
+    assert np.array_equal(a.act, act_before[a.ids])
+
+
+def test_reduce_removes_exactly_the_pairs_of_deleted_clauses():
+    inst = synth.tiny()
+    a = ActivityOracle(0.95)
+    a.add(inst.offsets, inst.lits)
+    full = oracle.pairs(inst.offsets, inst.lits, inst.codes)
+    a.after_test(full[:, 0])
+    a.reduce(0.5)
+    kept = set(a.ids.tolist())
+    want = full[[int(c) in kept for c in full[:, 0]]]
+    assert np.array_equal(a.pairs(inst.codes), want)
+    # clauses added after a reduction take new ids; ids are never reused
+    first = a.add(inst.offsets[:11], inst.lits[: int(inst.offsets[10])])
+    assert first == inst.n_clauses and a.ids[-1] == inst.n_clauses + 9
