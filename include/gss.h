@@ -103,6 +103,8 @@ typedef struct {
   uint64_t candidate_pairs; /* last test: (clause, 32-assignment group) pairs whose aggregate test
                                (Section 4.2) was positive; valid after gss_report_count / fetch */
   uint64_t group_pairs;     /* last test: n_clauses * ceil(N / 32), all (clause, group) pairs */
+  uint64_t clauses_removed; /* by gss_reduce_db, in total */
+  uint64_t next_clause_id;  /* id the next added clause gets (ids are never reused) */
 } gss_stats;
 
 /* ------------------------------------------------------------ lifecycle */
@@ -263,6 +265,43 @@ int gss_batch_fetch_reports(gss_batch* b, uint32_t instance, gss_report* out, ui
 
 int gss_batch_get_info(const gss_batch* b, gss_batch_info* out);
 const char* gss_batch_last_error(const gss_batch* b);
+
+/* ------------------------------------------- clause activity and deletion */
+
+/*
+ * Section 3.6: the GPU deletes clauses by activity, as MiniSat does on the CPU, and a
+ * clause's activity is bumped whenever it triggers.  The paper gives no constants; this
+ * library follows MiniSat:
+ *   - activities are single-precision floats; a clause starts at the current increment inc
+ *     (clauses already resident when activity is switched on start at inc = 1);
+ *   - each gss_test bumps every clause it reports (for any assignment) once: act += inc;
+ *   - after each gss_test, inc *= (1 / decay); once inc exceeds 1e20 all activities and inc
+ *     are multiplied by 1e-20.
+ * A test whose assignment set holds an invalid code bumps nothing.
+ */
+
+/* Switch activity on (0 < decay <= 1), or change the decay of an active context. */
+int gss_set_activity(gss_ctx* ctx, float decay);
+
+/* Activities of the resident clauses in clause order (as gss_get_clause_ids); *n_out = the
+ * number of resident clauses.  GSS_E_STATE if activity is off; GSS_E_OVERFLOW if cap is
+ * smaller (the first cap are written). */
+int gss_get_activity(gss_ctx* ctx, float* out, uint64_t cap, uint64_t* n_out);
+
+/* Ids of the resident clauses, increasing (ids are assigned by gss_add_clauses and never
+ * reused).  Errors as gss_get_activity. */
+int gss_get_clause_ids(gss_ctx* ctx, uint32_t* out, uint64_t cap, uint64_t* n_out);
+
+/*
+ * Remove floor(remove_fraction * n) of the n resident clauses longer than two literals:
+ * those with the smallest activity, ties broken by the smaller id (MiniSat removes the half
+ * of its learnt clauses with the lowest activity and keeps binary clauses).  Kept clauses keep
+ * their ids, activities and order; records of later tests carry the ids.  *n_removed
+ * (nullable) receives the count.  Needs activity on (GSS_E_STATE); GSS_E_NOMEM if the
+ * compacted copy does not fit (the database is then unchanged).  Records of an earlier test
+ * stay valid.
+ */
+int gss_reduce_db(gss_ctx* ctx, double remove_fraction, uint64_t* n_removed);
 
 /* ------------------------------------------------- without allocation */
 

@@ -42,7 +42,8 @@ class gss_stats(ctypes.Structure):
     _fields_ = [("n_vars", ctypes.c_uint32), ("n_assign", ctypes.c_uint32), ("n_clauses", ctypes.c_uint64),
                 ("n_lits", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64), ("report_capacity", ctypes.c_uint64),
                 ("tests_run", ctypes.c_uint64), ("pair_tests", ctypes.c_uint64),
-                ("candidate_pairs", ctypes.c_uint64), ("group_pairs", ctypes.c_uint64)]
+                ("candidate_pairs", ctypes.c_uint64), ("group_pairs", ctypes.c_uint64),
+                ("clauses_removed", ctypes.c_uint64), ("next_clause_id", ctypes.c_uint64)]
 
 
 class gss_batch_info(ctypes.Structure):
@@ -114,6 +115,10 @@ SIGNATURES = {
     "gss_batch_get_info": (i32, [P, P]),
     "gss_batch_last_error": (ctypes.c_char_p, [P]),
     "gss_test_noalloc": (i32, [P, u64, P, u32, P, u64, u32, u32, P, u64, P, P, P, ctypes.c_size_t]),
+    "gss_set_activity": (i32, [P, ctypes.c_float]),
+    "gss_get_activity": (i32, [P, P, u64, P]),
+    "gss_get_clause_ids": (i32, [P, P, u64, P]),
+    "gss_reduce_db": (i32, [P, ctypes.c_double, P]),
     "gss_server_config_init": (i32, [P]),
     "gss_server_create": (i32, [P, u32, P]),
     "gss_server_destroy": (i32, [P]),
@@ -330,6 +335,34 @@ class Context:
 
     def stats(self) -> dict:
         return gss_get_stats(self.ptr)
+
+    def set_activity(self, decay: float) -> None:
+        _check(self.ptr, load().gss_set_activity(self.ptr, decay))
+
+    def activity(self) -> np.ndarray:
+        n = ctypes.c_uint64()
+        rc = load().gss_get_activity(self.ptr, None, 0, ctypes.byref(n))
+        if rc not in (GSS_OK, GSS_E_OVERFLOW):
+            _check(self.ptr, rc)
+        out = np.empty(n.value, np.float32)
+        _check(self.ptr, load().gss_get_activity(self.ptr, ctypes.c_void_p(out.ctypes.data), len(out),
+                                                 ctypes.byref(n)))
+        return out
+
+    def clause_ids(self) -> np.ndarray:
+        n = ctypes.c_uint64()
+        rc = load().gss_get_clause_ids(self.ptr, None, 0, ctypes.byref(n))
+        if rc not in (GSS_OK, GSS_E_OVERFLOW):
+            _check(self.ptr, rc)
+        out = np.empty(n.value, np.uint32)
+        _check(self.ptr, load().gss_get_clause_ids(self.ptr, ctypes.c_void_p(out.ctypes.data), len(out),
+                                                   ctypes.byref(n)))
+        return out
+
+    def reduce_db(self, remove_fraction: float) -> int:
+        n = ctypes.c_uint64()
+        _check(self.ptr, load().gss_reduce_db(self.ptr, remove_fraction, ctypes.byref(n)))
+        return n.value
 
     def run(self, values) -> np.ndarray:
         """set_assignments + test + fetch_reports."""

@@ -252,16 +252,21 @@ int gss_add_clauses(gss_ctx* c, const uint64_t* offsets, uint64_t n, const uint3
   if (!c) return GSS_E_INVAL;
   c->err.clear();
   if (n == 0) {
-    if (first_id) *first_id = (uint32_t)c->m;
+    if (first_id) *first_id = (uint32_t)c->next_id;
     return GSS_OK;
   }
   if (!offsets) return fail(c, GSS_E_INVAL, "offsets is NULL");
   if (offsets[0] != 0) return fail(c, GSS_E_INVAL, "offsets[0] must be 0");
   const uint64_t L = offsets[n];
   if (L && !lits) return fail(c, GSS_E_INVAL, "lits is NULL");
-  if (c->m + n >= (1ull << 32)) return fail(c, GSS_E_INVAL, "more than 2^32 - 1 clauses");
+  if (c->next_id + n >= (1ull << 32)) return fail(c, GSS_E_INVAL, "more than 2^32 - 1 clauses");
   DeviceGuard dg(c->device);
   int rc;
+  if (c->act) {  // activities and bump stamps of the new clauses
+    if ((rc = grow(c, c->act, c->cap_act, c->m, c->m + n))) return rc;
+    if ((rc = grow(c, c->stamp, c->cap_stamp, c->m, c->m + n))) return rc;
+  }
+  if (c->ext && (rc = grow(c, c->ext, c->cap_ext, c->m, c->m + n))) return rc;
   // cap_m counts offsets entries (m + 1); head capacities count literals (8 per clause per plane)
   if ((rc = grow(c, c->off, c->cap_m, c->m + 1, c->m + n + 1))) return rc;
   if ((rc = grow(c, c->head0, c->cap_head0, c->m * 8, (c->m + n) * 8))) return rc;
@@ -295,9 +300,15 @@ int gss_add_clauses(gss_ctx* c, const uint64_t* offsets, uint64_t n, const uint3
   }
   if (c->map) CK(c, launch_translate(blits, L, c->map, c->stream));
   CK(c, launch_build_heads(c->boff, n, c->L, c->head0 + c->m * 8, c->head1 + c->m * 8, c->lits, c->V, c->stream));
-  if (first_id) *first_id = (uint32_t)c->m;
+  if (c->act) {  // a new clause starts at the current increment, as if bumped once
+    CK(c, launch_fill_f32(c->act + c->m, n, c->inc, c->stream));
+    CK(c, launch_fill_u32(c->stamp + c->m, n, 0xFFFFFFFFu, c->stream));
+  }
+  if (c->ext) CK(c, launch_iota_u32(c->ext + c->m, n, (uint32_t)c->next_id, c->stream));
+  if (first_id) *first_id = (uint32_t)c->next_id;
   c->m += n;
   c->L += L;
+  c->next_id += n;
   return GSS_OK;
 }
 
@@ -392,10 +403,20 @@ int gss_test(gss_ctx* c) {
   DeviceGuard dg(c->device);
   CK(c, cudaMemsetAsync(&c->st->n_records, 0, 2 * sizeof(unsigned long long), c->stream));  // records, candidates
   if (c->m && c->N) {
-    ClauseView db{c->off, c->lits, c->head0, c->head1, 2u * c->V};
+    ClauseView db{c->off, c->lits, c->head0, c->head1, 2u * c->V, c->ext};
     PlaneView pv{c->P, c->aggF, c->aggU, c->Wp, c->AWp, c->N};
+    ActivityView av;
+    if (c->act) av = ActivityView{c->act, c->stamp, c->epoch, c->inc};
     CK(c, launch_test((int)c->mode, db, 0, c->m, pv, c->rec, c->rec_cap, c->st, launch_grid(c, c->mode, c->AWp),
-                      c->stream));
+                      c->stream, nullptr, 0, av));
+  }
+  if (c->act) {  // after the test's bumps: the increment grows by 1 / decay, rescaled past 1e20
+    c->epoch = c->epoch + 1 == 0xFFFFFFFFu ? 0 : c->epoch + 1;
+    c->inc = c->inc * c->inv_decay;
+    if (c->inc > 1e20f) {
+      CK(c, launch_scale_f32(c->act, c->m, 1e-20f, c->stream));
+      c->inc = c->inc * 1e-20f;
+    }
   }
   c->tested = true;
   c->tests_run += 1;
@@ -503,6 +524,8 @@ int gss_get_stats(const gss_ctx* c, gss_stats* o) {
   o->tests_run = c->tests_run;
   o->pair_tests = c->pair_tests;
   o->candidate_pairs = c->tested ? c->h_st[0].n_candidates : 0;
+  o->clauses_removed = c->removed;
+  o->next_clause_id = c->next_id;
   o->group_pairs = c->tested ? c->m * (uint64_t)((c->N + 31) / 32) : 0;
   return GSS_OK;
 }

@@ -27,6 +27,16 @@ struct gss_ctx {
   uint32_t* head1 = nullptr;
   uint64_t* boff = nullptr;
   uint32_t* map = nullptr;  // internal variable ids (frequency layout), fixed by the first batch
+  uint64_t next_id = 0;     // id of the next clause added; ids are never reused
+  uint32_t* ext = nullptr;  // id of each resident clause, once a reduction has removed some (else: position)
+  uint64_t cap_ext = 0, removed = 0;
+
+  // clause activity (Section 3.6), off until gss_set_activity
+  float* act = nullptr;
+  uint32_t* stamp = nullptr;  // test epoch that last bumped the clause
+  uint64_t cap_act = 0, cap_stamp = 0;
+  float decay = 1.0f, inv_decay = 1.0f, inc = 1.0f;
+  uint32_t epoch = 0;
 
   // assignment set
   uint32_t N = 0, Wp = 4, AWp = 1;

@@ -51,6 +51,16 @@ struct ClauseView {
   const uint32_t* head0;
   const uint32_t* head1;
   uint32_t pad;  // PAD literal = 2V
+  const uint32_t* ext = nullptr;  // caller-visible id of each resident clause (nullptr: its position)
+};
+
+// Clause activity (Section 3.6): during a test, each reported clause gets act += inc once;
+// stamp[c] == epoch marks a clause already bumped by this test.  act == nullptr: off.
+struct ActivityView {
+  float* act = nullptr;
+  uint32_t* stamp = nullptr;
+  uint32_t epoch = 0;
+  float inc = 0.0f;
 };
 
 // ---------------------------------------------------------------- launchers
@@ -82,7 +92,7 @@ cudaError_t launch_build_heads(const uint64_t* boff, uint64_t n, uint64_t L0, ui
 // entries, non-decreasing), clause c is tested against plane word w only if c < wm[w].
 cudaError_t launch_test(int mode, const ClauseView& db, uint64_t c_lo, uint64_t c_hi, const PlaneView& pv,
                         gss_report* rec, uint64_t cap, DevStatus* st, int grid, cudaStream_t s,
-                        const uint64_t* wm = nullptr, uint32_t n_wm = 0);
+                        const uint64_t* wm = nullptr, uint32_t n_wm = 0, const ActivityView& av = ActivityView{});
 
 // Group a serving launch's records by plane word (request) into out: records of word w at
 // [sum of count[0..w), + count[w]), their mask ANDed with nmask[w], records left without a bit
@@ -91,6 +101,28 @@ cudaError_t launch_test(int mode, const ClauseView& db, uint64_t c_lo, uint64_t 
 cudaError_t launch_route(const gss_report* rec, const DevStatus* st, uint64_t cap, const uint32_t* nmask, uint32_t k,
                          unsigned long long* count, unsigned long long* cursor, gss_report* out, int grid,
                          cudaStream_t s);
+
+// ---------------------------------------------------------------- clause activity and deletion (k_reduce.cu)
+cudaError_t launch_fill_u32(uint32_t* p, uint64_t n, uint32_t value, cudaStream_t s);
+cudaError_t launch_fill_f32(float* p, uint64_t n, float value, cudaStream_t s);
+cudaError_t launch_iota_u32(uint32_t* p, uint64_t n, uint32_t first, cudaStream_t s);
+cudaError_t launch_scale_f32(float* p, uint64_t n, float factor, cudaStream_t s);
+// Histogram of the 8 key bits at `shift` over the clauses longer than two literals whose key
+// agrees with `prefix` above shift + 8; key = (bits of act) << 32 | id.  hist: 256 counters (zeroed here).
+cudaError_t launch_key_hist(const uint64_t* off, const float* act, const uint32_t* ids, uint64_t m, uint32_t shift,
+                            uint64_t prefix, uint32_t* hist, cudaStream_t s);
+// Compact the database: clause c is kept iff it has at most two literals or its key > kmax.
+// The plan scans keep flags and kept sizes into scratch (compact_scratch_bytes(m)) and writes
+// the kept clauses and literals to d_counts[0..1]; the copy then moves the kept clauses, in
+// order, into the n* arrays sized for them (noff[0] is left to the caller).
+uint64_t compact_scratch_bytes(uint64_t m);
+cudaError_t launch_compact_plan(const uint64_t* off, const float* act, const uint32_t* ids, uint64_t m, uint64_t kmax,
+                                void* scratch, unsigned long long* d_counts, cudaStream_t s);
+cudaError_t launch_compact_copy(const uint64_t* off, const uint32_t* lits, const uint32_t* head0,
+                                const uint32_t* head1, const float* act, const uint32_t* stamp, const uint32_t* ids,
+                                uint64_t m, uint64_t kmax, const void* scratch, uint64_t* noff, uint32_t* nlits,
+                                uint32_t* nhead0, uint32_t* nhead1, float* nact, uint32_t* nstamp, uint32_t* nids,
+                                cudaStream_t s);
 
 // Occupancy-derived persistent grid for launch_test on this device.
 int test_grid_size(int mode, uint32_t AWp, int n_sms);

@@ -283,11 +283,14 @@ __device__ __forceinline__ void live_words(const uint64_t* wm, uint32_t n_wm, ui
 }
 
 // Stage A and stage B for the tile of clauses [c0, min(c0 + 32, c_hi)), whose head0 is in
-// S.ring[s]; records are staged in the warp's outbox.
-template <int MODE, int AW>
+// S.ring[s]; records are staged in the warp's outbox.  EXTRA: the database has clause ids
+// apart from positions and/or activities to bump (a separate build of the kernel, so that
+// databases without them pay nothing).
+template <int MODE, int AW, bool EXTRA = false>
 __device__ __forceinline__ void test_tile(const ClauseView& db, const PlaneView& pv, const HotRows& hot, WarpSmem& S,
                                           int s, uint64_t c0, uint64_t c_hi, uint32_t lane, Outbox& out,
-                                          const uint64_t* wm = nullptr, uint32_t n_wm = 0) {
+                                          const uint64_t* wm = nullptr, uint32_t n_wm = 0,
+                                          const ActivityView& av = ActivityView{}) {
   const uint32_t PAD = db.pad;
   const uint64_t c = c0 + lane;
   const bool act = c < c_hi;
@@ -295,8 +298,8 @@ __device__ __forceinline__ void test_tile(const ClauseView& db, const PlaneView&
 
   // ---------------- stage A: group (aggregate) test of this lane's clause
   uint32_t af[AW], ou[AW];
-#pragma unroll
   live_words<AW>(wm, n_wm, c, af);
+#pragma unroll
   for (int i = 0; i < AW; ++i) { af[i] = act ? af[i] : 0u; ou[i] = 0u; }
   if (act) {
     uint32_t l[8], l1[8];
@@ -360,16 +363,24 @@ __device__ __forceinline__ void test_tile(const ClauseView& db, const PlaneView&
       word_batch8<MODE>(pv, la, ga, va, afa, oua);
       exact_tail<MODE>(db, pv, c0 + oa, ga, va, la[7], afa, oua);
       const uint32_t ra = afa | oua;
-      out_append(S, out, ra != 0u, (uint32_t)(c0 + oa), ga, ra, lane);
+      const uint64_t cp = c0 + oa;  // position of the pair's clause
+      uint32_t id = (uint32_t)cp;
+      if constexpr (EXTRA) {
+        if (ra != 0u && av.act && atomicExch(av.stamp + cp, av.epoch) != av.epoch)
+          av.act[cp] += av.inc;  // bumped once per test, by the first of its reported pairs
+        if (db.ext) id = __ldg(db.ext + cp);
+      }
+      out_append(S, out, ra != 0u, id, ga, ra, lane);
     }
     __syncwarp();
   }
 }
 
-template <int MODE, int AW>
+template <int MODE, int AW, bool EXTRA>
 __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c_lo, uint64_t c_hi, PlaneView pv,
                                                        gss_report* __restrict__ rec, uint64_t cap, DevStatus* st,
-                                                       const uint64_t* __restrict__ wm, uint32_t n_wm) {
+                                                       const uint64_t* __restrict__ wm, uint32_t n_wm,
+                                                       ActivityView av) {
   __shared__ WarpSmem smem[TEST_WARPS];
   __shared__ uint64_t s_wm[32 * AW];  // per-word clause watermarks (serving launches)
   __shared__ __align__(16) uint32_t hotF[HOT_WORDS];
@@ -426,7 +437,7 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c
       out_close(S, out, lane);
       return;
     }
-    test_tile<MODE, AW>(db, pv, hot, S, s, c_lo + t * 32u, c_hi, lane, out, wms, n_wm);
+    test_tile<MODE, AW, EXTRA>(db, pv, hot, S, s, c_lo + t * 32u, c_hi, lane, out, wms, n_wm, av);
     __syncwarp();
   }
   out_close(S, out, lane);
@@ -535,14 +546,16 @@ __global__ void k_batch_reset(const BatchInst* __restrict__ inst, uint32_t n_ins
 
 template <int MODE, int AW>
 void launch_one(const ClauseView& db, uint64_t c_lo, uint64_t c_hi, const PlaneView& pv, gss_report* rec,
-                uint64_t cap, DevStatus* st, int grid, cudaStream_t s, const uint64_t* wm, uint32_t n_wm) {
-  k_test<MODE, AW><<<grid, TEST_THREADS, 0, s>>>(db, c_lo, c_hi, pv, rec, cap, st, wm, n_wm);
+                uint64_t cap, DevStatus* st, int grid, cudaStream_t s, const uint64_t* wm, uint32_t n_wm,
+                const ActivityView& av) {
+  if (db.ext || av.act) k_test<MODE, AW, true><<<grid, TEST_THREADS, 0, s>>>(db, c_lo, c_hi, pv, rec, cap, st, wm, n_wm, av);
+  else k_test<MODE, AW, false><<<grid, TEST_THREADS, 0, s>>>(db, c_lo, c_hi, pv, rec, cap, st, wm, n_wm, av);
 }
 
 template <int MODE, int AW>
 int grid_for(int n_sms) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_test<MODE, AW>, TEST_THREADS, 0) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_test<MODE, AW, false>, TEST_THREADS, 0) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
   return per_sm * n_sms;
@@ -597,20 +610,20 @@ int test_batch_grid_size(int mode, uint32_t AWp, int n_sms) {
 
 cudaError_t launch_test(int mode, const ClauseView& db, uint64_t c_lo, uint64_t c_hi, const PlaneView& pv,
                         gss_report* rec, uint64_t cap, DevStatus* st, int grid, cudaStream_t s, const uint64_t* wm,
-                        uint32_t n_wm) {
+                        uint32_t n_wm, const ActivityView& av) {
   if (c_hi <= c_lo) return cudaSuccess;
   const uint64_t tiles = (c_hi - c_lo + 31) / 32;
   const uint64_t max_blocks = (tiles + TEST_WARPS - 1) / TEST_WARPS;
   if ((uint64_t)grid > max_blocks) grid = (int)max_blocks;
   if (grid < 1) grid = 1;
   if (mode == GSS_MODE_ALLF) {
-    if (pv.AWp == 1) launch_one<GSS_MODE_ALLF, 1>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm);
-    else if (pv.AWp == 2) launch_one<GSS_MODE_ALLF, 2>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm);
-    else launch_one<GSS_MODE_ALLF, 4>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm);
+    if (pv.AWp == 1) launch_one<GSS_MODE_ALLF, 1>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av);
+    else if (pv.AWp == 2) launch_one<GSS_MODE_ALLF, 2>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av);
+    else launch_one<GSS_MODE_ALLF, 4>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av);
   } else {
-    if (pv.AWp == 1) launch_one<GSS_MODE_TRIGGER, 1>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm);
-    else if (pv.AWp == 2) launch_one<GSS_MODE_TRIGGER, 2>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm);
-    else launch_one<GSS_MODE_TRIGGER, 4>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm);
+    if (pv.AWp == 1) launch_one<GSS_MODE_TRIGGER, 1>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av);
+    else if (pv.AWp == 2) launch_one<GSS_MODE_TRIGGER, 2>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av);
+    else launch_one<GSS_MODE_TRIGGER, 4>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av);
   }
   return cudaGetLastError();
 }
