@@ -32,10 +32,10 @@
 // The PAD literal 2V is neutral in both modes: its P and aggF rows are all ones and its
 // aggU row is zero, so padded head slots need no branch.
 //
-// The internal variable numbering puts the hottest variables first (see k_ingest.cu); the
-// aggregate rows of the 2048 lowest literal ids (8 KiB) are copied into shared memory once
-// per block and serve most stage-A gathers under Zipf-distributed variables (the
-// shared-memory reuse of hot variables proposed in Section 7).
+// The internal variable numbering puts the hottest variables first (see k_ingest.cu), so
+// the aggregate rows gathered most often share a few cache lines and stay in L1.  (A copy
+// of those rows in shared memory was measured: 182 us against 171 us without it on the
+// 4M-clause workload, so the L1 serves them better.)
 #include "gss_internal.h"
 #include "gss_ptx.h"
 
@@ -47,7 +47,6 @@ constexpr int TEST_THREADS = 256;
 constexpr int TEST_WARPS = TEST_THREADS / 32;
 constexpr uint32_t PAIR_CAP = 64;        // candidate pairs staged per warp per round
 constexpr uint32_t OUT_CAP = 64;         // records staged per warp before one reservation
-constexpr uint32_t HOT_WORDS = 2048;     // shared words for the hottest aggF rows (8 KiB)
 
 struct __align__(128) WarpSmem {
   uint32_t ring[2][32 * 8];  // head0 of the current and the next tile
@@ -77,25 +76,6 @@ __device__ __forceinline__ void load_agg(const uint32_t* __restrict__ base, uint
   }
 }
 
-// Aggregate row `row` (AW words): rows below n_hot come from the block's shared copy.
-template <int AW>
-__device__ __forceinline__ void load_agg_cached(const uint32_t* __restrict__ base, const uint32_t* hot, uint32_t n_hot,
-                                                uint32_t row, uint32_t (&r)[AW]) {
-  if (row < n_hot) {
-    if constexpr (AW == 1) {
-      r[0] = hot[row];
-    } else if constexpr (AW == 2) {
-      const uint2 t = reinterpret_cast<const uint2*>(hot)[row];
-      r[0] = t.x; r[1] = t.y;
-    } else {
-      const uint4 t = reinterpret_cast<const uint4*>(hot)[row];
-      r[0] = t.x; r[1] = t.y; r[2] = t.z; r[3] = t.w;
-    }
-  } else {
-    load_agg<AW>(base, row, r);
-  }
-}
-
 template <int AW>
 __device__ __forceinline__ bool any2(const uint32_t (&a)[AW], const uint32_t (&b)[AW]) {
   uint32_t o = 0;
@@ -105,21 +85,16 @@ __device__ __forceinline__ bool any2(const uint32_t (&a)[AW], const uint32_t (&b
 }
 
 // Stage A on 8 literals: gathers first, then the recurrence in order.
-struct HotRows {  // the block's shared copies of the hottest aggregate rows
-  const uint32_t* F;
-  const uint32_t* U;
-  uint32_t nF, nU;
-};
 
 template <int MODE, int AW>
-__device__ __forceinline__ void group_batch8(const PlaneView& pv, const HotRows& hot, const uint32_t (&l)[8],
+__device__ __forceinline__ void group_batch8(const PlaneView& pv, const uint32_t (&l)[8],
                                              uint32_t (&af)[AW], uint32_t (&ou)[AW]) {
   constexpr int B = (AW == 4) ? 4 : 8;  // literals per sub-batch (bounds registers for wide rows)
 #pragma unroll
   for (int j0 = 0; j0 < 8; j0 += B) {
     uint32_t cf[B][AW];
 #pragma unroll
-    for (int j = 0; j < B; ++j) load_agg_cached<AW>(pv.aggF, hot.F, hot.nF, l[j0 + j], cf[j]);
+    for (int j = 0; j < B; ++j) load_agg<AW>(pv.aggF, l[j0 + j], cf[j]);
     if constexpr (MODE == GSS_MODE_ALLF) {
 #pragma unroll
       for (int j = 0; j < B; ++j)
@@ -128,7 +103,7 @@ __device__ __forceinline__ void group_batch8(const PlaneView& pv, const HotRows&
     } else {
       uint32_t cu[B][AW];
 #pragma unroll
-      for (int j = 0; j < B; ++j) load_agg_cached<AW>(pv.aggU, hot.U, hot.nU, l[j0 + j] >> 1, cu[j]);
+      for (int j = 0; j < B; ++j) load_agg<AW>(pv.aggU, l[j0 + j] >> 1, cu[j]);
 #pragma unroll
       for (int j = 0; j < B; ++j)
 #pragma unroll
@@ -287,7 +262,7 @@ __device__ __forceinline__ void live_words(const uint64_t* wm, uint32_t n_wm, ui
 // apart from positions and/or activities to bump (a separate build of the kernel, so that
 // databases without them pay nothing).
 template <int MODE, int AW, bool EXTRA = false>
-__device__ __forceinline__ void test_tile(const ClauseView& db, const PlaneView& pv, const HotRows& hot, WarpSmem& S,
+__device__ __forceinline__ void test_tile(const ClauseView& db, const PlaneView& pv, WarpSmem& S,
                                           int s, uint64_t c0, uint64_t c_hi, uint32_t lane, Outbox& out,
                                           const uint64_t* wm = nullptr, uint32_t n_wm = 0,
                                           const ActivityView& av = ActivityView{}) {
@@ -308,14 +283,14 @@ __device__ __forceinline__ void test_tile(const ClauseView& db, const PlaneView&
     l[4] = b.x; l[5] = b.y; l[6] = b.z; l[7] = b.w;
     const bool long_clause = l[7] != PAD;
     if (long_clause) load8_global(db.head1 + c * 8u, l1);  // in flight during the first batch
-    group_batch8<MODE, AW>(pv, hot, l, af, ou);
+    group_batch8<MODE, AW>(pv, l, af, ou);
     if (long_clause && any2<AW>(af, ou)) {
-      group_batch8<MODE, AW>(pv, hot, l1, af, ou);
+      group_batch8<MODE, AW>(pv, l1, af, ou);
       if (l1[7] != PAD && any2<AW>(af, ou)) {
         const uint64_t e = db.off[c + 1];
         for (uint64_t k0 = db.off[c] + HEAD_K; k0 < e && any2<AW>(af, ou); k0 += 8) {
           load8_csr(db.lits, k0, e, PAD, l);
-          group_batch8<MODE, AW>(pv, hot, l, af, ou);
+          group_batch8<MODE, AW>(pv, l, af, ou);
         }
       }
     }
@@ -383,17 +358,7 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c
                                                        ActivityView av) {
   __shared__ WarpSmem smem[TEST_WARPS];
   __shared__ uint64_t s_wm[32 * AW];  // per-word clause watermarks (serving launches)
-  __shared__ __align__(16) uint32_t hotF[HOT_WORDS];
-  __shared__ __align__(16) uint32_t hotU[MODE == GSS_MODE_TRIGGER ? HOT_WORDS / 2 : 4];
   if (st->bad_code) return;  // the assignment set held an invalid value code: no records
-  const uint32_t PAD = db.pad;
-  HotRows hot;
-  hot.nF = min((uint32_t)(HOT_WORDS / AW), PAD + 2u);  // literal rows 0 .. 2V + 1 exist
-  hot.nU = MODE == GSS_MODE_TRIGGER ? min((uint32_t)(HOT_WORDS / 2 / AW), PAD / 2u + 1u) : 0u;
-  for (uint32_t i = threadIdx.x; i < hot.nF * AW; i += TEST_THREADS) hotF[i] = __ldg(pv.aggF + i);
-  for (uint32_t i = threadIdx.x; i < hot.nU * AW; i += TEST_THREADS) hotU[i] = __ldg(pv.aggU + i);
-  hot.F = hotF;
-  hot.U = hotU;
   if (n_wm > 32u * AW) n_wm = 32u * AW;
   for (uint32_t i = threadIdx.x; wm && i < n_wm; i += TEST_THREADS) s_wm[i] = wm[i];
   __syncthreads();
@@ -437,7 +402,7 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c
       out_close(S, out, lane);
       return;
     }
-    test_tile<MODE, AW, EXTRA>(db, pv, hot, S, s, c_lo + t * 32u, c_hi, lane, out, wms, n_wm, av);
+    test_tile<MODE, AW, EXTRA>(db, pv, S, s, c_lo + t * 32u, c_hi, lane, out, wms, n_wm, av);
     __syncwarp();
   }
   out_close(S, out, lane);
@@ -466,9 +431,6 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test_batch(const BatchInst* __
   __shared__ WarpSmem smem[TEST_WARPS];
   const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
   WarpSmem& S = smem[wib];
-  HotRows hot;  // rows differ between instances: no shared copy
-  hot.F = hot.U = nullptr;
-  hot.nF = hot.nU = 0;
   unsigned long long cb = 0;
   if (lane == 0) cb = atomicAdd(work, (unsigned long long)grab);
   cb = __shfl_sync(FULL, cb, 0);
@@ -524,7 +486,7 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test_batch(const BatchInst* __
       cur = i;
     }
     if (!st->bad_code)
-      test_tile<MODE, AW>(db, pv, hot, S, s, (t - inst[i].tile0) * 32u, inst[i].m, lane, out);
+      test_tile<MODE, AW>(db, pv, S, s, (t - inst[i].tile0) * 32u, inst[i].m, lane, out);
     __syncwarp();  // every lane is done with ring[s] before it is refilled
     if (!has_next) break;
     t = tn;
