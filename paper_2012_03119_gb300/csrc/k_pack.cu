@@ -48,18 +48,23 @@ constexpr int PK_CONSUMERS = 4;
 constexpr int PK_DEPTH = 1;
 constexpr int PK_MINB = 4;
 constexpr int PK_BOX = PK_VT * PK_ROWS;            // 4 KiB
-constexpr int PK_STRIDE = 2 * PK_VT + 1;           // staged words per plane word (odd)
+// Staged words of a pass: row r = 2 vl + s (variable vl of the tile, literal sign s) holds
+// its 32 plane words, word wl at r * 32 + (wl ^ stage_swizzle(r)).  The swizzle makes both
+// the transposition's stores (32 lanes: rows 8 lane + c, one word) and the write-out's loads
+// (4 consecutive rows x 8 word quads) free of bank conflicts.
 constexpr uint32_t BAR_CONSUMERS = 1;              // named barrier of the consumer warps
 
 template <int C, int D>
 struct PackSmem {
   uint8_t ring[C * D][PK_BOX];
-  uint32_t stage[32 * PK_STRIDE];
+  uint32_t stage[2 * PK_VT * 32];
   uint32_t rowid[PK_VT];  // internal id of each variable of the current tile
   uint32_t aggw[3 * PK_VT];  // aggregate bits of the pass: aggF rows (2 vl, 2 vl + 1), then aggU (vl)
   unsigned long long full[C * D], empty[C * D];
   volatile int err;
 };
+
+__device__ __forceinline__ uint32_t stage_swizzle(uint32_t r) { return ((r >> 3) + (r & 3u)) & 31u; }
 
 __device__ __forceinline__ uint32_t valid_bits(uint32_t N, uint32_t w) {
   const uint32_t lo = w * 32u;
@@ -211,11 +216,11 @@ __global__ void __launch_bounds__(32 * (C + 1), MINB) k_pack(const __grid_consta
         x[5] = __byte_perm(tc, td, 0x5410);
         x[6] = __byte_perm(fc, fd, 0x7632);
         x[7] = __byte_perm(tc, td, 0x7632);
-        uint32_t* sw = S.stage + wl * PK_STRIDE + lane;
         const uint32_t bit = 1u << wl, vw = valid_bits(N, w);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          sw[j * 32] = x[j];
+          const uint32_t r = 8u * lane + (uint32_t)j;  // row of (variable 4 lane + j / 2, sign j % 2)
+          S.stage[r * 32u + (wl ^ stage_swizzle(r))] = x[j];
           aF[j] |= x[j] != 0u ? bit : 0u;  // F is in G(l)
         }
 #pragma unroll
@@ -229,18 +234,21 @@ __global__ void __launch_bounds__(32 * (C + 1), MINB) k_pack(const __grid_consta
         if (aU[k]) atomicOr(&S.aggw[2u * PK_VT + vl], aU[k]);
       }
       ptx::named_bar_sync(BAR_CONSUMERS, 32 * C);
-      // coalesced write-out over (variable, word) pairs, word index fastest
-      const uint32_t total = PK_VT * nw;  // a multiple of 32: every lane runs the same trip count
+      // coalesced write-out: one 16-byte store per 4 words of a row, quads fastest
+      const uint32_t lg_nq = lg_nw - 2u;  // nw >= 4
+      const uint32_t total = 2u * PK_VT << lg_nq;
       for (uint32_t i = threadIdx.x; i < total; i += 32 * C) {
-        const uint32_t vl = i >> lg_nw, wl = i & (nw - 1u);
-        const uint32_t kv = vl & 3u, ln = vl >> 2;
-        const uint32_t Fw = S.stage[wl * PK_STRIDE + (2u * kv) * 32u + ln];
-        const uint32_t Tw = S.stage[wl * PK_STRIDE + (2u * kv + 1u) * 32u + ln];
-        const uint32_t w = wc + wl;
+        const uint32_t r = i >> lg_nq, q = i & ((1u << lg_nq) - 1u);
+        const uint32_t vl = r >> 1, sw = stage_swizzle(r);
+        const uint32_t* row = S.stage + r * 32u;
+        uint4 x4;
+        x4.x = row[(4u * q) ^ sw];
+        x4.y = row[(4u * q + 1u) ^ sw];
+        x4.z = row[(4u * q + 2u) ^ sw];
+        x4.w = row[(4u * q + 3u) ^ sw];
         if (vl < nv) {
           const uint64_t v = S.rowid[vl];  // internal row of variable v0 + vl
-          P[(2u * v) * Wp + w] = Fw;
-          P[(2u * v + 1u) * Wp + w] = Tw;
+          *reinterpret_cast<uint4*>(P + (2u * v + (r & 1u)) * Wp + wc + 4u * q) = x4;
         }
       }
       if (threadIdx.x < PK_VT) {  // one aggregate word per row and pass; cleared for the next pass
