@@ -47,6 +47,7 @@ constexpr int PK_ROWS = 32;                        // assignment rows per box: o
 constexpr int PK_CONSUMERS = 4;
 constexpr int PK_DEPTH = 1;
 constexpr int PK_MINB = 4;
+constexpr int PK_PASS = 32;  // plane words staged per pass (a variable's row is written in pieces of this width)
 constexpr int PK_BOX = PK_VT * PK_ROWS;            // 4 KiB
 // Staged words of a pass: row r = 2 vl + s (variable vl of the tile, literal sign s) holds
 // its 32 plane words, word wl at r * 32 + (wl ^ stage_swizzle(r)).  The swizzle makes both
@@ -54,10 +55,10 @@ constexpr int PK_BOX = PK_VT * PK_ROWS;            // 4 KiB
 // (4 consecutive rows x 8 word quads) free of bank conflicts.
 constexpr uint32_t BAR_CONSUMERS = 1;              // named barrier of the consumer warps
 
-template <int C, int D>
+template <int C, int D, int PW>
 struct PackSmem {
   uint8_t ring[C * D][PK_BOX];
-  uint32_t stage[2 * PK_VT * 32];
+  uint32_t stage[2 * PK_VT * PW];
   uint32_t rowid[PK_VT];  // internal id of each variable of the current tile
   uint32_t aggw[3 * PK_VT];  // aggregate bits of the pass: aggF rows (2 vl, 2 vl + 1), then aggU (vl)
   unsigned long long full[C * D], empty[C * D];
@@ -88,7 +89,7 @@ __device__ __forceinline__ uint32_t stage_of(uint32_t q, uint32_t t, uint32_t w,
   return q + C * (word_seq<C>(q, t, w, Wd, b, g) % D);
 }
 
-template <int C, int D, int MINB>
+template <int C, int D, int MINB, int PW>
 __global__ void __launch_bounds__(32 * (C + 1), MINB) k_pack(const __grid_constant__ CUtensorMap tmap, uint32_t V,
                                                         uint32_t N, uint32_t Wp, uint32_t AWp,
                                                         const uint32_t* __restrict__ map,
@@ -97,8 +98,9 @@ __global__ void __launch_bounds__(32 * (C + 1), MINB) k_pack(const __grid_consta
                                                         uint32_t* __restrict__ aggU, DevStatus* st) {
   // the consumer threads load the row ids of a whole tile: one thread per variable
   static_assert(32 * C >= PK_VT, "k_pack needs at least PK_VT / 32 consumer warps");
+  static_assert(PW >= 4 && PW <= 32 && (PW & (PW - 1)) == 0 && PW % C == 0, "pass width");
   extern __shared__ uint8_t smem_raw[];
-  PackSmem<C, D>& S = *reinterpret_cast<PackSmem<C, D>*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  PackSmem<C, D, PW>& S = *reinterpret_cast<PackSmem<C, D, PW>*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   const uint32_t n_vt = (V + PK_VT - 1) / PK_VT;
   const uint32_t Wd = (N + 31) / 32;  // plane words that hold assignments
@@ -159,8 +161,8 @@ __global__ void __launch_bounds__(32 * (C + 1), MINB) k_pack(const __grid_consta
   for (uint32_t t = blockIdx.x; t < n_vt; t += gridDim.x) {
     const uint32_t v0 = t * PK_VT;
     const uint32_t nv = min((uint32_t)PK_VT, V - v0);
-    for (uint32_t wc = 0; wc < Wp; wc += 32u) {
-      const uint32_t nw = min(32u, Wp - wc);  // 4, 8, 16 or 32 words in this pass (one aggregate word)
+    for (uint32_t wc = 0; wc < Wp; wc += PW) {
+      const uint32_t nw = min((uint32_t)PW, Wp - wc);  // 4 .. PW words in this pass
       const uint32_t lg_nw = 31u - __clz(nw);
       if (wc == 0 && threadIdx.x < PK_VT) {  // read by the write-out after the next barrier
         S.rowid[threadIdx.x] = next_row;
@@ -216,11 +218,11 @@ __global__ void __launch_bounds__(32 * (C + 1), MINB) k_pack(const __grid_consta
         x[5] = __byte_perm(tc, td, 0x5410);
         x[6] = __byte_perm(fc, fd, 0x7632);
         x[7] = __byte_perm(tc, td, 0x7632);
-        const uint32_t bit = 1u << wl, vw = valid_bits(N, w);
+        const uint32_t bit = 1u << (w & 31u), vw = valid_bits(N, w);  // bit of the word in its aggregate word
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const uint32_t r = 8u * lane + (uint32_t)j;  // row of (variable 4 lane + j / 2, sign j % 2)
-          S.stage[r * 32u + (wl ^ stage_swizzle(r))] = x[j];
+          S.stage[r * PW + (wl ^ (stage_swizzle(r) & (PW - 1u)))] = x[j];
           aF[j] |= x[j] != 0u ? bit : 0u;  // F is in G(l)
         }
 #pragma unroll
@@ -239,8 +241,8 @@ __global__ void __launch_bounds__(32 * (C + 1), MINB) k_pack(const __grid_consta
       const uint32_t total = 2u * PK_VT << lg_nq;
       for (uint32_t i = threadIdx.x; i < total; i += 32 * C) {
         const uint32_t r = i >> lg_nq, q = i & ((1u << lg_nq) - 1u);
-        const uint32_t vl = r >> 1, sw = stage_swizzle(r);
-        const uint32_t* row = S.stage + r * 32u;
+        const uint32_t vl = r >> 1, sw = stage_swizzle(r) & (PW - 1u);
+        const uint32_t* row = S.stage + r * PW;
         uint4 x4;
         x4.x = row[(4u * q) ^ sw];
         x4.y = row[(4u * q + 1u) ^ sw];
@@ -251,7 +253,8 @@ __global__ void __launch_bounds__(32 * (C + 1), MINB) k_pack(const __grid_consta
           *reinterpret_cast<uint4*>(P + (2u * v + (r & 1u)) * Wp + wc + 4u * q) = x4;
         }
       }
-      if (threadIdx.x < PK_VT) {  // one aggregate word per row and pass; cleared for the next pass
+      const bool agg_done = ((wc + nw) & 31u) == 0u || wc + nw >= Wp;  // the pass ends an aggregate word
+      if (agg_done && threadIdx.x < PK_VT) {  // one aggregate word per row; cleared for the next one
         const uint32_t vl = threadIdx.x;
         const uint32_t gF = S.aggw[2u * vl], gT = S.aggw[2u * vl + 1u], gU = S.aggw[2u * PK_VT + vl];
         S.aggw[2u * vl] = 0u;
@@ -284,16 +287,17 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // Launch k_pack<C, D, MINB> over every variable tile: MINB persistent CTAs per SM.
-template <int C, int D, int MINB>
+template <int C, int D, int MINB, int PW = PK_PASS>
 cudaError_t launch_pack_cfg(const CUtensorMap& tmap, uint32_t V, uint32_t N, uint32_t Wp, uint32_t AWp,
                             const uint32_t* map, const uint32_t* word_rows, uint32_t* P, uint32_t* aggF,
                             uint32_t* aggU, DevStatus* st, cudaStream_t s) {
-  const size_t smem = sizeof(PackSmem<C, D>) + 128;
+  const size_t smem = sizeof(PackSmem<C, D, PW>) + 128;
   int dev = 0, n_sms = 1;
   cudaGetDevice(&dev);
   static std::atomic<bool> smem_set[64];  // once per device, before any graph capture that packs
   if (dev < 0 || dev >= 64 || !smem_set[dev].load(std::memory_order_acquire)) {
-    const cudaError_t e = cudaFuncSetAttribute(k_pack<C, D, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_pack<C, D, MINB, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) smem_set[dev].store(true, std::memory_order_release);
   }
@@ -301,7 +305,7 @@ cudaError_t launch_pack_cfg(const CUtensorMap& tmap, uint32_t V, uint32_t N, uin
   const uint32_t n_vt = (V + PK_VT - 1) / PK_VT;
   const uint32_t slots = (uint32_t)MINB * (uint32_t)n_sms;
   const uint32_t grid = n_vt < slots ? n_vt : slots;
-  k_pack<C, D, MINB><<<grid, 32 * (C + 1), smem, s>>>(tmap, V, N, Wp, AWp, map, word_rows, P, aggF, aggU, st);
+  k_pack<C, D, MINB, PW><<<grid, 32 * (C + 1), smem, s>>>(tmap, V, N, Wp, AWp, map, word_rows, P, aggF, aggU, st);
   return cudaGetLastError();
 }
 
