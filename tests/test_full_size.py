@@ -43,3 +43,52 @@ def test_structured_full_size_sampled():
     for i in rng.choice(len(got), size=min(2000, len(got)), replace=False):
         c, a = got[i]
         assert oracle.pair(inst.offsets, inst.lits, inst.codes[a], int(c))
+
+
+def test_batch_full_size():
+    """The 64-instance batching workload at full size (18.6M clauses, 12.5 G pair tests) in one
+    graph run: every instance's planted pairs are found, and 17 instances (the largest, the
+    smallest and a spread between them) equal the oracle in full."""
+    insts = [synth.batch_instance(sp) for sp in synth.batch_specs(64)]
+    with gss.Batch() as b:
+        for I in insts:
+            cap = I.n_clauses * ((I.n_assign + 31) // 32) // 4 + 65536
+            i = b.add_instance(I.n_vars, I.offsets, I.lits, max_assignments=I.n_assign, report_capacity=cap)
+            b.set_assignments(i, I.codes)
+        b.test()
+        got = [gss.expand_reports(b.fetch_reports(i)) for i in range(len(insts))]
+    by_size = sorted(range(len(insts)), key=lambda i: insts[i].n_clauses * insts[i].n_assign)
+    full = set(by_size[:: max(1, len(by_size) // 14)]) | {by_size[0], by_size[-1]}
+    for i, (I, g) in enumerate(zip(insts, got)):
+        s = set(map(tuple, g.tolist()))
+        assert all(tuple(p) in s for p in I.planted.tolist()), I.name
+        assert len(g) == 0 or (g[:, 0].max() < I.n_clauses and g[:, 1].max() < I.n_assign)
+        if i in full:
+            want = oracle.allf_pairs(I.offsets, I.lits, I.codes)
+            assert g.shape == want.shape and np.array_equal(g, want), I.name
+
+
+def test_serve_full_size():
+    """The serving workload's database (1M vars, 2M clauses growing by 50k batches) with the
+    bench's server shape; requests admitted between batches are checked against the oracle on
+    the database prefix their watermark names."""
+    w = synth.serve_workload(scale=1.0, n_batches=6)
+    snaps = synth.serve_snapshots(w.n_vars, 4, seed=synth.seed_for(4, 1))
+    final = len(w.offsets) - 1
+    with gss.Server(w.n_vars, max_clauses=final + 1, max_lits=int(w.offsets[-1]) + 1, slots=64, lanes=3,
+                    lane_report_capacity=1 << 23) as srv:
+        srv.add_clauses(*w.csr(0, w.n_initial))
+        ids = [(srv.submit(snaps[0], wait_us=10_000_000), 0)]
+        for b in range(w.n_batches):
+            srv.add_clauses(*w.csr(*w.batch_range(b)))
+            ids.append((srv.submit(snaps[(b + 1) % 4], wait_us=10_000_000), (b + 1) % 4))
+        results = [(srv.wait(rid), k) for rid, k in ids]
+    seen = set()
+    for (rec, info), k in results:
+        wm = info["watermark"]
+        assert w.n_initial <= wm <= final
+        off = w.offsets[: wm + 1]
+        want = oracle.allf_pairs(off, w.lits[: int(off[-1])], snaps[k])
+        assert np.array_equal(gss.expand_reports(rec), want)
+        seen.add(wm)
+    assert len(seen) > 1  # requests saw different database sizes
