@@ -105,6 +105,8 @@ typedef struct {
   uint64_t group_pairs;     /* last test: n_clauses * ceil(N / 32), all (clause, group) pairs */
   uint64_t clauses_removed; /* by gss_reduce_db, in total */
   uint64_t next_clause_id;  /* id the next added clause gets (ids are never reused) */
+  uint64_t records;         /* records produced by the tests whose results were read, in total */
+  uint64_t overflows;       /* of those tests, how many produced more records than the capacity */
 } gss_stats;
 
 /* ------------------------------------------------------------ lifecycle */
@@ -303,6 +305,16 @@ int gss_get_clause_ids(gss_ctx* ctx, uint32_t* out, uint64_t cap, uint64_t* n_ou
  */
 int gss_reduce_db(gss_ctx* ctx, double remove_fraction, uint64_t* n_removed);
 
+/*
+ * Copy the resident clauses out, in the caller's variable numbering: offsets[0..n] (CSR,
+ * offsets[0] = 0), lits[0..L) and, if ids is not NULL, their ids[0..n), in the order of
+ * gss_get_clause_ids.  *n_clauses / *n_lits (nullable) receive n and L; with cap_clauses < n
+ * or cap_lits < L nothing is copied and GSS_E_OVERFLOW is returned.  Feeding the export to
+ * gss_add_clauses of a new context rebuilds the database (new ids count from 0).
+ */
+int gss_export_clauses(gss_ctx* ctx, uint64_t* offsets, uint64_t cap_clauses, uint32_t* lits, uint64_t cap_lits,
+                       uint32_t* ids, uint64_t* n_clauses, uint64_t* n_lits);
+
 /* ------------------------------------------------- without allocation */
 
 /*
@@ -388,6 +400,9 @@ typedef struct {
   uint64_t slot_memory_bytes;    /* non-zero: slots = min(slots, slot_memory_bytes / slot size) */
   uint32_t tests_in_flight;      /* launches whose test kernels may overlap (default 1; 0: lanes) */
   uint32_t pad;
+  uint64_t result_ttl_us;        /* kept results not taken by gss_server_wait within this time after
+                                    completion are dropped (a client that died; checked about every
+                                    10-100 ms); 0: kept forever */
 } gss_server_config;
 
 /* Flags of gss_server_submit. */
@@ -412,6 +427,7 @@ typedef struct {
   uint64_t pair_tests;                    /* sum over completed requests of watermark * n_assign */
   uint64_t reports;                       /* records delivered (after dropping padded assignments) */
   uint64_t committed_clauses;
+  uint64_t expired;                       /* kept results dropped after result_ttl_us */
   uint32_t slots, pad;
   double p50_us, p99_us, max_us, mean_us; /* latency of completed requests */
 } gss_server_stats;
@@ -457,6 +473,16 @@ int gss_server_get_stats(gss_server* srv, gss_server_stats* out);
 const char* gss_server_last_error(const gss_server* srv);
 
 /* ---------------------------------------------------------- diagnostics */
+
+/*
+ * The bounds-checked build (compiled with GSS_DEBUG_BOUNDS; the Python binding loads it when
+ * the environment variable GSS_DEBUG_BOUNDS=1 is set) checks, in the test kernels, every
+ * plane row index before gathering with it; an index out of range is counted on the device
+ * and replaced by the neutral PAD row.  *enabled = 1 in that build (0 otherwise, *errors = 0);
+ * *errors = violations counted on the current device since the last reset (reset != 0
+ * zeroes the counter).  Synchronises the device.
+ */
+int gss_debug_bounds(uint32_t* enabled, uint64_t* errors, int reset);
 
 int gss_get_stats(const gss_ctx* ctx, gss_stats* out);
 

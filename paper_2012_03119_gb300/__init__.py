@@ -43,7 +43,8 @@ class gss_stats(ctypes.Structure):
                 ("n_lits", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64), ("report_capacity", ctypes.c_uint64),
                 ("tests_run", ctypes.c_uint64), ("pair_tests", ctypes.c_uint64),
                 ("candidate_pairs", ctypes.c_uint64), ("group_pairs", ctypes.c_uint64),
-                ("clauses_removed", ctypes.c_uint64), ("next_clause_id", ctypes.c_uint64)]
+                ("clauses_removed", ctypes.c_uint64), ("next_clause_id", ctypes.c_uint64),
+                ("records", ctypes.c_uint64), ("overflows", ctypes.c_uint64)]
 
 
 class gss_batch_info(ctypes.Structure):
@@ -57,7 +58,7 @@ class gss_server_config(ctypes.Structure):
                 ("max_clauses", ctypes.c_uint64), ("max_lits", ctypes.c_uint64), ("slots", ctypes.c_uint32),
                 ("lanes", ctypes.c_uint32), ("lane_report_capacity", ctypes.c_uint64),
                 ("slot_memory_bytes", ctypes.c_uint64), ("tests_in_flight", ctypes.c_uint32),
-                ("pad", ctypes.c_uint32)]
+                ("pad", ctypes.c_uint32), ("result_ttl_us", ctypes.c_uint64)]
 
 
 class gss_request_info(ctypes.Structure):
@@ -69,7 +70,8 @@ class gss_request_info(ctypes.Structure):
 class gss_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("dropped", ctypes.c_uint64), ("completed", ctypes.c_uint64),
                 ("launches", ctypes.c_uint64), ("words_launched", ctypes.c_uint64), ("pair_tests", ctypes.c_uint64),
-                ("reports", ctypes.c_uint64), ("committed_clauses", ctypes.c_uint64), ("slots", ctypes.c_uint32),
+                ("reports", ctypes.c_uint64), ("committed_clauses", ctypes.c_uint64), ("expired", ctypes.c_uint64),
+                ("slots", ctypes.c_uint32),
                 ("pad", ctypes.c_uint32), ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
                 ("max_us", ctypes.c_double), ("mean_us", ctypes.c_double)]
 
@@ -119,6 +121,8 @@ SIGNATURES = {
     "gss_get_activity": (i32, [P, P, u64, P]),
     "gss_get_clause_ids": (i32, [P, P, u64, P]),
     "gss_reduce_db": (i32, [P, ctypes.c_double, P]),
+    "gss_export_clauses": (i32, [P, P, u64, P, u64, P, P, P]),
+    "gss_debug_bounds": (i32, [P, P, i32]),
     "gss_server_config_init": (i32, [P]),
     "gss_server_create": (i32, [P, u32, P]),
     "gss_server_destroy": (i32, [P]),
@@ -268,6 +272,15 @@ def gss_test_noalloc(d_offsets: int, n_clauses: int, d_lits: int, n_vars: int, d
         raise GssError(rc, buf.value.decode())
 
 
+def gss_debug_bounds(reset: bool = False) -> tuple[bool, int]:
+    """(bounds-checked build?, index violations counted on the current device)."""
+    en, n = ctypes.c_uint32(), ctypes.c_uint64()
+    rc = load().gss_debug_bounds(ctypes.byref(en), ctypes.byref(n), 1 if reset else 0)
+    if rc != GSS_OK:
+        raise GssError(rc, "gss_debug_bounds failed")
+    return bool(en.value), n.value
+
+
 def gss_strerror(code: int) -> str:
     return load().gss_strerror(code).decode()
 
@@ -358,6 +371,20 @@ class Context:
         _check(self.ptr, load().gss_get_clause_ids(self.ptr, ctypes.c_void_p(out.ctypes.data), len(out),
                                                    ctypes.byref(n)))
         return out
+
+    def export_clauses(self):
+        """(offsets, lits, ids) of the resident clauses, in the caller's variable numbering."""
+        n, L = ctypes.c_uint64(), ctypes.c_uint64()
+        rc = load().gss_export_clauses(self.ptr, None, 0, None, 0, None, ctypes.byref(n), ctypes.byref(L))
+        if rc not in (GSS_OK, GSS_E_OVERFLOW):
+            _check(self.ptr, rc)
+        off = np.empty(n.value + 1, np.uint64)
+        lits = np.empty(max(1, L.value), np.uint32)
+        ids = np.empty(max(1, n.value), np.uint32)
+        _check(self.ptr, load().gss_export_clauses(self.ptr, ctypes.c_void_p(off.ctypes.data), n.value,
+                                                   ctypes.c_void_p(lits.ctypes.data), L.value,
+                                                   ctypes.c_void_p(ids.ctypes.data), ctypes.byref(n), ctypes.byref(L)))
+        return off, lits[: L.value], ids[: n.value]
 
     def reduce_db(self, remove_fraction: float) -> int:
         n = ctypes.c_uint64()
@@ -488,13 +515,15 @@ class Server:
 
     def __init__(self, n_vars: int, device: int = 0, mode: int = GSS_MODE_ALLF, layout: int = GSS_LAYOUT_FREQUENCY,
                  max_clauses: int = 1 << 20, max_lits: int = 1 << 24, slots: int = 64, lanes: int = 3,
-                 lane_report_capacity: int = 1 << 20, slot_memory_bytes: int = 0, tests_in_flight: int = 1):
+                 lane_report_capacity: int = 1 << 20, slot_memory_bytes: int = 0, tests_in_flight: int = 1,
+                 result_ttl_us: int = 0):
         cfg = gss_server_config()
         load().gss_server_config_init(ctypes.byref(cfg))
         cfg.device, cfg.mode, cfg.layout = device, mode, layout
         cfg.max_clauses, cfg.max_lits, cfg.slots, cfg.lanes = max_clauses, max_lits, slots, lanes
         cfg.lane_report_capacity, cfg.slot_memory_bytes = lane_report_capacity, slot_memory_bytes
         cfg.tests_in_flight = tests_in_flight
+        cfg.result_ttl_us = result_ttl_us
         self.n_vars = n_vars
         self.ptr = ctypes.c_void_p()
         rc = load().gss_server_create(ctypes.byref(self.ptr), n_vars, ctypes.byref(cfg))

@@ -11,8 +11,11 @@ from concurrent.futures import ThreadPoolExecutor
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
-OUT_DIR = os.path.join(PKG, "_build")
-LIB = os.path.join(PKG, "libgss.so")
+# GSS_DEBUG_BOUNDS=1 selects a separate, bounds-checked build (the kernels check every index
+# they gather with and count violations instead of reading out of range).
+BOUNDS = os.environ.get("GSS_DEBUG_BOUNDS", "") not in ("", "0")
+OUT_DIR = os.path.join(PKG, "_build_bounds" if BOUNDS else "_build")
+LIB = os.path.join(PKG, "libgss_bounds.so" if BOUNDS else "libgss.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 
@@ -40,6 +43,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
         if not force and up_to_date():
             return LIB
         flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
+        if BOUNDS:
+            flags += ["-DGSS_DEBUG_BOUNDS"]
         if ptxas_verbose:
             flags += ["-Xptxas", "-v"]
 

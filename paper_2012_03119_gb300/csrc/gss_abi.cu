@@ -250,6 +250,7 @@ int gss_destroy(gss_ctx* c) {
 
 int gss_add_clauses(gss_ctx* c, const uint64_t* offsets, uint64_t n, const uint32_t* lits, uint32_t* first_id) {
   if (!c) return GSS_E_INVAL;
+  TraceRange tr("gss_add_clauses");
   c->err.clear();
   if (n == 0) {
     if (first_id) *first_id = (uint32_t)c->next_id;
@@ -382,6 +383,7 @@ int pack_staged(gss_ctx* c, cudaStream_t s) {
 extern "C" {
 
 static int set_assignments_common(gss_ctx* c, const uint8_t* src, uint64_t pitch, uint32_t n, bool device_src) {
+  TraceRange tr("gss_set_assignments (pack)");
   int rc = stage_assignments(c, src, pitch, n, device_src);
   if (rc) return rc;
   DeviceGuard dg(c->device);
@@ -398,13 +400,14 @@ int gss_set_assignments_device(gss_ctx* c, const uint8_t* d_values, uint64_t pit
 
 int gss_test(gss_ctx* c) {
   if (!c) return GSS_E_INVAL;
+  TraceRange tr("gss_test");
   c->err.clear();
   if (!c->have_assign) return fail(c, GSS_E_STATE, "gss_test before gss_set_assignments");
   DeviceGuard dg(c->device);
   CK(c, cudaMemsetAsync(&c->st->n_records, 0, 2 * sizeof(unsigned long long), c->stream));  // records, candidates
   if (c->m && c->N) {
     ClauseView db{c->off, c->lits, c->head0, c->head1, 2u * c->V, c->ext};
-    PlaneView pv{c->P, c->aggF, c->aggU, c->Wp, c->AWp, c->N};
+    PlaneView pv{c->P, c->aggF, c->aggU, c->Wp, c->AWp, c->N, c->V};
     ActivityView av;
     if (c->act) av = ActivityView{c->act, c->stamp, c->epoch, c->inc};
     CK(c, launch_test((int)c->mode, db, 0, c->m, pv, c->rec, c->rec_cap, c->st, launch_grid(c, c->mode, c->AWp),
@@ -419,6 +422,7 @@ int gss_test(gss_ctx* c) {
     }
   }
   c->tested = true;
+  c->counted = false;
   c->tests_run += 1;
   c->pair_tests += c->m * (uint64_t)c->N;
   return GSS_OK;
@@ -441,6 +445,11 @@ int wait_test(gss_ctx* c, uint64_t* n, bool sync) {
     return fail(c, GSS_E_TIMEOUT, "a bounded device wait gave up; the records of this test are incomplete");
   }
   *n = c->h_st[0].n_records;
+  if (!c->counted) {
+    c->counted = true;
+    c->records += *n;
+    c->overflows += *n > c->rec_cap ? 1 : 0;
+  }
   return GSS_OK;
 }
 }  // namespace host
@@ -449,6 +458,7 @@ int wait_test(gss_ctx* c, uint64_t* n, bool sync) {
 extern "C" {
 
 int gss_fetch_reports(gss_ctx* c, gss_report* out, uint64_t cap, uint64_t* n_out) {
+  TraceRange tr("gss_fetch_reports");
   if (!c || (cap && !out)) return c ? fail(c, GSS_E_INVAL, "out is NULL") : GSS_E_INVAL;
   c->err.clear();
   DeviceGuard dg(c->device);
@@ -513,6 +523,21 @@ int gss_set_mode(gss_ctx* c, uint32_t mode) {
   return GSS_OK;
 }
 
+int gss_debug_bounds(uint32_t* enabled, uint64_t* errors, int reset) {
+#ifdef GSS_DEBUG_BOUNDS
+  if (enabled) *enabled = 1;
+#else
+  if (enabled) *enabled = 0;
+#endif
+  unsigned long long n = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess || debug_bounds_errors(&n, reset != 0) != cudaSuccess) {
+    cudaGetLastError();
+    return GSS_E_CUDA;
+  }
+  if (errors) *errors = n;
+  return GSS_OK;
+}
+
 int gss_get_stats(const gss_ctx* c, gss_stats* o) {
   if (!c || !o) return GSS_E_INVAL;
   o->n_vars = c->V;
@@ -525,6 +550,8 @@ int gss_get_stats(const gss_ctx* c, gss_stats* o) {
   o->pair_tests = c->pair_tests;
   o->candidate_pairs = c->tested ? c->h_st[0].n_candidates : 0;
   o->clauses_removed = c->removed;
+  o->records = c->records;
+  o->overflows = c->overflows;
   o->next_clause_id = c->next_id;
   o->group_pairs = c->tested ? c->m * (uint64_t)((c->N + 31) / 32) : 0;
   return GSS_OK;

@@ -1,4 +1,5 @@
-// gss_activity.cu -- clause activity and activity-based deletion on a context (Section 3.6:
+// gss_activity.cu -- database upkeep on a context: clause activity and activity-based
+// deletion (Section 3.6:
 // the GPU, like the CPU solvers, has to delete clauses or it would slow down and run out of
 // memory; it deletes by activity as MiniSat does, and bumps a clause whenever it triggers).
 //
@@ -7,6 +8,7 @@
 // it passes 1e20 (see gss_test).  gss_reduce_db removes the requested fraction of the
 // clauses longer than two literals with the smallest (activity, id) and compacts the
 // database in place of the old arrays; ids stay with their clauses and are never reused.
+// gss_export_clauses copies the resident database back out in the caller's numbering.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -111,6 +113,7 @@ int gss_get_clause_ids(gss_ctx* c, uint32_t* out, uint64_t cap, uint64_t* n_out)
 
 int gss_reduce_db(gss_ctx* c, double remove_fraction, uint64_t* n_removed) {
   if (!c) return GSS_E_INVAL;
+  TraceRange tr("gss_reduce_db");
   c->err.clear();
   if (n_removed) *n_removed = 0;
   if (!(remove_fraction >= 0.0 && remove_fraction <= 1.0)) return fail(c, GSS_E_INVAL, "fraction outside [0, 1]");
@@ -233,6 +236,48 @@ int gss_reduce_db(gss_ctx* c, double remove_fraction, uint64_t* n_removed) {
   c->L = nL;
   c->removed += n_remove;
   if (n_removed) *n_removed = n_remove;
+  return GSS_OK;
+}
+
+int gss_export_clauses(gss_ctx* c, uint64_t* offsets, uint64_t cap_clauses, uint32_t* lits, uint64_t cap_lits,
+                       uint32_t* ids, uint64_t* n_clauses, uint64_t* n_lits) {
+  if (!c) return GSS_E_INVAL;
+  c->err.clear();
+  if (n_clauses) *n_clauses = c->m;
+  if (n_lits) *n_lits = c->L;
+  if (cap_clauses < c->m || cap_lits < c->L)
+    return fail(c, GSS_E_OVERFLOW, "%llu clauses, %llu literals to export", (unsigned long long)c->m,
+                (unsigned long long)c->L);
+  if (!offsets || (c->L && !lits)) return fail(c, GSS_E_INVAL, "offsets / lits is NULL");
+  Guard g(c->device);
+  ACK(cudaMemcpyAsync(offsets, c->off, (c->m + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, c->stream));
+  if (c->L) {
+    if (c->map) {  // literals back in the caller's variable numbering
+      uint32_t *tmp = nullptr, *inv = nullptr;
+      int rc;
+      if ((rc = alloc(c, tmp, c->L))) return rc;
+      if ((rc = alloc(c, inv, c->V))) {
+        dev_free(c, tmp);
+        return rc;
+      }
+      cudaError_t e = cudaMemcpyAsync(tmp, c->lits, c->L * sizeof(uint32_t), cudaMemcpyDeviceToDevice, c->stream);
+      if (e == cudaSuccess) e = launch_invert_u32(c->map, c->V, inv, c->stream);
+      if (e == cudaSuccess) e = launch_translate(tmp, c->L, inv, c->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(lits, tmp, c->L * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      dev_free(c, tmp);
+      dev_free(c, inv);
+      if (e != cudaSuccess) return fail(c, GSS_E_CUDA, "export: %s", cudaGetErrorString(e));
+    } else {
+      ACK(cudaMemcpyAsync(lits, c->lits, c->L * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    }
+  }
+  ACK(cudaStreamSynchronize(c->stream));
+  if (ids) {
+    uint64_t n = 0;
+    const int rc = gss_get_clause_ids(c, ids, c->m, &n);
+    if (rc) return rc;
+  }
   return GSS_OK;
 }
 

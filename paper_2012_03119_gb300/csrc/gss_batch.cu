@@ -137,7 +137,7 @@ int build_groups(gss_batch* b) {
       gss_ctx* c = b->inst[i];
       BatchInst d{};
       d.db = ClauseView{c->off, c->lits, c->head0, c->head1, 2u * c->V};
-      d.pv = PlaneView{c->P, c->aggF, c->aggU, c->Wp, c->AWp, c->N};
+      d.pv = PlaneView{c->P, c->aggF, c->aggU, c->Wp, c->AWp, c->N, c->V};
       d.m = c->N ? c->m : 0;  // an empty assignment set has nothing to test
       d.tile0 = tiles;
       d.rec = c->rec;
@@ -376,6 +376,7 @@ int gss_batch_set_assignments_device(gss_batch* b, uint32_t i, const uint8_t* d_
 }
 
 int gss_batch_test(gss_batch* b) {
+  TraceRange tr("gss_batch_test");
   if (!b) return GSS_E_INVAL;
   b->err.clear();
   if (b->inst.empty()) return bfail(b, GSS_E_STATE, "the batch has no instances");

@@ -2,6 +2,7 @@
 // and batch (gss_batch.cu) host code.  Not part of the public interface.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <string>
 #include <unordered_map>
@@ -59,11 +60,21 @@ struct gss_ctx {
   int grid[2][5] = {{0}};     // cached persistent grid per (mode, AWp)
 
   uint64_t tests_run = 0, pair_tests = 0;
+  uint64_t records = 0, overflows = 0;  // of tests whose status was read
+  bool counted = false;                 // the last test's records are in `records`
   std::string err;
 };
 
 namespace gss {
 namespace host {
+
+// A named NVTX range around an entry point, for timeline tools; free when no tool listens.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 int fail(gss_ctx* c, int code, const char* fmt, ...);
 int dev_alloc(gss_ctx* c, void** p, uint64_t bytes);

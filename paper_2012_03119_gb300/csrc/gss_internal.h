@@ -42,7 +42,12 @@ struct PlaneView {
   const uint32_t* aggF;
   const uint32_t* aggU;
   uint32_t Wp, AWp, N;
+  uint32_t V;  // rows: P and aggF 2V + 2, aggU V + 1
 };
+
+// Bounds-checked build (GSS_DEBUG_BOUNDS): the test kernels check every row they gather from
+// and count violations in a device counter, reading the neutral PAD row instead.
+cudaError_t debug_bounds_errors(unsigned long long* out, bool reset);  // 0 when not built in
 
 // Clause database (device pointers).
 struct ClauseView {
@@ -107,6 +112,8 @@ cudaError_t launch_fill_u32(uint32_t* p, uint64_t n, uint32_t value, cudaStream_
 cudaError_t launch_fill_f32(float* p, uint64_t n, float value, cudaStream_t s);
 cudaError_t launch_iota_u32(uint32_t* p, uint64_t n, uint32_t first, cudaStream_t s);
 cudaError_t launch_scale_f32(float* p, uint64_t n, float factor, cudaStream_t s);
+// inv[map[i]] = i for i < n (map a permutation of [0, n)).
+cudaError_t launch_invert_u32(const uint32_t* map, uint32_t n, uint32_t* inv, cudaStream_t s);
 // Histogram of the 8 key bits at `shift` over the clauses longer than two literals whose key
 // agrees with `prefix` above shift + 8; key = (bits of act) << 32 | id.  hist: 256 counters (zeroed here).
 cudaError_t launch_key_hist(const uint64_t* off, const float* act, const uint32_t* ids, uint64_t m, uint32_t shift,

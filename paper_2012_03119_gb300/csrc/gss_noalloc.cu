@@ -137,7 +137,7 @@ extern "C" int gss_test_noalloc(const uint64_t* d_offsets, uint64_t n_clauses, c
   int n_sms = 1;
   cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev);
   const ClauseView db{off, d_lits, head0, head1, 2u * n_vars};
-  const PlaneView pv{P, aggF, aggU, Wp, AWp, n_assign};
+  const PlaneView pv{P, aggF, aggU, Wp, AWp, n_assign, n_vars};
   NA_CK(launch_test((int)mode, db, 0, n_clauses, pv, d_out, cap, st, test_grid_size((int)mode, AWp, n_sms), s));
   NA_CK(cudaMemcpyAsync(d_count, &st->n_records, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
   NA_CK(cudaMemcpyAsync(h, st, sizeof h, cudaMemcpyDeviceToHost, s));

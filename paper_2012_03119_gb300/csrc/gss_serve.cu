@@ -57,6 +57,7 @@ struct Request {
   uint32_t slot = 0, n = 0;
   uint64_t wm = 0;
   bool keep = false, done = false, overflow = false, bad = false;
+  uint32_t waiters = 0;  // clients inside gss_server_wait on it: never dropped meanwhile
   uint32_t batch_words = 0;
   Clock::time_point t_submit, t_admit, t_launch, t_done;
   std::vector<gss_report> recs;
@@ -105,6 +106,8 @@ struct gss_server {
   std::vector<Lane> lanes;  // sized once at creation (lanes are not movable)
   int grid = 0, route_grid = 0;
   uint32_t tests_in_flight = 1;  // launches whose test may overlap
+  uint64_t ttl_us = 0;           // kept results older than this are dropped (0: never)
+  Clock::time_point last_sweep;
 
   std::mutex mu, ingest_mu;
   std::condition_variable cv_slot, cv_done;
@@ -123,6 +126,7 @@ struct gss_server {
   bool wake = false;
 
   uint64_t submitted = 0, dropped = 0, completed = 0, launches = 0, words = 0, pair_tests = 0, reports = 0;
+  uint64_t expired = 0;
   std::vector<double> lat_us;
   std::mutex err_mu;
   std::string err;
@@ -166,6 +170,7 @@ void CUDART_CB lane_done(void* p) {
 
 // Start a launch on lane L with the oldest admitted requests (v->mu held).
 cudaError_t start_launch(gss_server* v, Lane& L) {
+  TraceRange tr("gss_server launch");
   const uint32_t k = (uint32_t)std::min<size_t>(32, v->ready.size());
   L.ids.assign(v->ready.begin(), v->ready.begin() + k);
   v->ready.erase(v->ready.begin(), v->ready.begin() + k);
@@ -197,7 +202,7 @@ cudaError_t start_launch(gss_server* v, Lane& L) {
     e = launch_pack_rows(v->d_slots, v->Vp, v->V, N, Wp, AWp, v->map.load(), L.d_in->rows, v->n_slots * 32u, L.P,
                          L.aggF, L.aggU, &L.d_out->pack_st, L.s);
   if (e == cudaSuccess && max_wm) {
-    const PlaneView pv{L.P, L.aggF, L.aggU, Wp, AWp, N};
+    const PlaneView pv{L.P, L.aggF, L.aggU, Wp, AWp, N, v->V};
     e = launch_test((int)v->mode, v->db, 0, max_wm, pv, L.rec, L.cap, &L.d_out->st, v->grid, L.s, L.d_in->wm, k);
   }
   if (e == cudaSuccess) e = cudaLaunchHostFunc(L.s, lane_tested, &L);
@@ -275,6 +280,21 @@ void scheduler(gss_server* v) {
         v->sched_err = GSS_E_CUDA;
         v->sched_msg = cudaGetErrorString(e);
         v->stop = true;
+      }
+    }
+    if (v->ttl_us) {  // drop kept results whose client has not taken them in time (a dead solver thread)
+      const Clock::time_point now = Clock::now();
+      if (now - v->last_sweep > std::chrono::milliseconds(10)) {
+        v->last_sweep = now;
+        for (auto it = v->reqs.begin(); it != v->reqs.end();) {
+          const Request& q = it->second;
+          if (q.done && q.waiters == 0 && now - q.t_done > std::chrono::microseconds(v->ttl_us)) {
+            it = v->reqs.erase(it);
+            v->expired += 1;
+          } else {
+            ++it;
+          }
+        }
       }
     }
     if (v->stop) {  // on destroy, let launches in flight finish; on an error, leave now
@@ -421,6 +441,8 @@ int gss_server_create(gss_server** out, uint32_t n_vars, const gss_server_config
   v->grid = test_grid_size((int)cfg.mode, 1, v->ctx->n_sms);
   v->route_grid = 2 * v->ctx->n_sms;
   v->tests_in_flight = cfg.tests_in_flight ? cfg.tests_in_flight : cfg.lanes;
+  v->ttl_us = cfg.result_ttl_us;
+  v->last_sweep = Clock::now();
   v->sched = std::thread(scheduler, v);
   *out = v;
   return GSS_OK;
@@ -507,8 +529,10 @@ int gss_server_wait(gss_server* v, uint64_t id, int64_t wait_us, gss_report* out
   Request* rp = &it->second;  // element references survive rehashing by other submits; iterators do not
   auto finished = [&] { return rp->done || v->sched_err != GSS_OK || v->closed; };
   if (!finished()) {
+    rp->waiters += 1;
     if (wait_us < 0) v->cv_done.wait(lk, finished);
     else v->cv_done.wait_for(lk, std::chrono::microseconds(wait_us), finished);
+    rp->waiters -= 1;
   }
   if (!rp->done) {
     if (v->sched_err) return sfail(v, v->sched_err, "scheduler stopped: %s", v->sched_msg.c_str());
@@ -552,6 +576,7 @@ int gss_server_get_stats(gss_server* v, gss_server_stats* o) {
     o->pair_tests = v->pair_tests;
     o->reports = v->reports;
     o->committed_clauses = v->committed.load();
+    o->expired = v->expired;
     o->slots = v->n_slots;
     l = v->lat_us;
   }

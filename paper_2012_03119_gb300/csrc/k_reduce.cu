@@ -34,6 +34,10 @@ __global__ void k_iota_u32(uint32_t* p, uint64_t n, uint32_t first) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
     p[i] = first + (uint32_t)i;
 }
+__global__ void k_invert_u32(const uint32_t* __restrict__ map, uint32_t n, uint32_t* __restrict__ inv) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    inv[map[i]] = (uint32_t)i;
+}
 __global__ void k_scale_f32(float* p, uint64_t n, float f) {
   for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
     p[i] = p[i] * f;
@@ -195,6 +199,10 @@ cudaError_t launch_fill_f32(float* p, uint64_t n, float v, cudaStream_t s) {
 }
 cudaError_t launch_iota_u32(uint32_t* p, uint64_t n, uint32_t first, cudaStream_t s) {
   if (n) k_iota_u32<<<grid_of(n, 256), 256, 0, s>>>(p, n, first);
+  return cudaGetLastError();
+}
+cudaError_t launch_invert_u32(const uint32_t* map, uint32_t n, uint32_t* inv, cudaStream_t s) {
+  if (n) k_invert_u32<<<grid_of(n, 256), 256, 0, s>>>(map, n, inv);
   return cudaGetLastError();
 }
 cudaError_t launch_scale_f32(float* p, uint64_t n, float f, cudaStream_t s) {

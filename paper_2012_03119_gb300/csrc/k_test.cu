@@ -63,6 +63,19 @@ __device__ __forceinline__ uint32_t valid_bits(uint32_t N, uint32_t w) {
   return rem >= 32u ? FULL : ((1u << rem) - 1u);
 }
 
+#ifdef GSS_DEBUG_BOUNDS
+__device__ unsigned long long g_bounds_errors;  // rows out of range met by the test kernels
+// row if row < rows, else the PAD row (rows - 2 for literal rows, rows - 1 for variable rows) and a count
+__device__ __forceinline__ uint32_t checked_row(uint32_t row, uint32_t rows, uint32_t pad_row) {
+  if (row < rows) return row;
+  atomicAdd(&g_bounds_errors, 1ull);
+  return pad_row;
+}
+#define GSS_ROW(row, rows, pad_row) checked_row((row), (rows), (pad_row))
+#else
+#define GSS_ROW(row, rows, pad_row) (row)
+#endif
+
 template <int AW>
 __device__ __forceinline__ void load_agg(const uint32_t* __restrict__ base, uint32_t row, uint32_t (&r)[AW]) {
   if constexpr (AW == 1) {
@@ -94,7 +107,7 @@ __device__ __forceinline__ void group_batch8(const PlaneView& pv, const uint32_t
   for (int j0 = 0; j0 < 8; j0 += B) {
     uint32_t cf[B][AW];
 #pragma unroll
-    for (int j = 0; j < B; ++j) load_agg<AW>(pv.aggF, l[j0 + j], cf[j]);
+    for (int j = 0; j < B; ++j) load_agg<AW>(pv.aggF, GSS_ROW(l[j0 + j], 2u * pv.V + 2u, 2u * pv.V), cf[j]);
     if constexpr (MODE == GSS_MODE_ALLF) {
 #pragma unroll
       for (int j = 0; j < B; ++j)
@@ -103,7 +116,7 @@ __device__ __forceinline__ void group_batch8(const PlaneView& pv, const uint32_t
     } else {
       uint32_t cu[B][AW];
 #pragma unroll
-      for (int j = 0; j < B; ++j) load_agg<AW>(pv.aggU, l[j0 + j] >> 1, cu[j]);
+      for (int j = 0; j < B; ++j) load_agg<AW>(pv.aggU, GSS_ROW(l[j0 + j] >> 1, pv.V + 1u, pv.V), cu[j]);
 #pragma unroll
       for (int j = 0; j < B; ++j)
 #pragma unroll
@@ -121,14 +134,14 @@ __device__ __forceinline__ void word_batch8(const PlaneView& pv, const uint32_t 
                                             uint32_t& af, uint32_t& ou) {
   uint32_t F[8];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) F[j] = __ldg(pv.P + (uint64_t)l[j] * pv.Wp + g);
+  for (int j = 0; j < 8; ++j) F[j] = __ldg(pv.P + (uint64_t)GSS_ROW(l[j], 2u * pv.V + 2u, 2u * pv.V) * pv.Wp + g);
   if constexpr (MODE == GSS_MODE_ALLF) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) af &= F[j];
   } else {
     uint32_t T[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) T[j] = __ldg(pv.P + (uint64_t)(l[j] ^ 1u) * pv.Wp + g);
+    for (int j = 0; j < 8; ++j) T[j] = __ldg(pv.P + (uint64_t)GSS_ROW(l[j] ^ 1u, 2u * pv.V + 2u, 2u * pv.V) * pv.Wp + g);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const uint32_t U = ~(F[j] | T[j]) & valid;
@@ -599,6 +612,21 @@ int test_grid_size(int mode, uint32_t AWp, int n_sms) {
   if (AWp == 1) return grid_for<GSS_MODE_TRIGGER, 1>(n_sms);
   if (AWp == 2) return grid_for<GSS_MODE_TRIGGER, 2>(n_sms);
   return grid_for<GSS_MODE_TRIGGER, 4>(n_sms);
+}
+
+cudaError_t debug_bounds_errors(unsigned long long* out, bool reset) {
+#ifdef GSS_DEBUG_BOUNDS
+  cudaError_t e = cudaMemcpyFromSymbol(out, g_bounds_errors, sizeof(unsigned long long));
+  if (e == cudaSuccess && reset) {
+    const unsigned long long zero = 0;
+    e = cudaMemcpyToSymbol(g_bounds_errors, &zero, sizeof zero);
+  }
+  return e;
+#else
+  (void)reset;
+  *out = 0;
+  return cudaSuccess;
+#endif
 }
 
 }  // namespace gss

@@ -29,6 +29,23 @@ def check_records(rec, m, N):
     assert len(np.unique(key)) == len(key), "duplicate (clause, word) record"
 
 
+def pair_keys(pairs):
+    """(clause, assignment) pairs as sorted uint64 keys."""
+    p = np.asarray(pairs).reshape(-1, 2)
+    return np.sort((p[:, 0].astype(np.uint64) << np.uint64(32)) | p[:, 1].astype(np.uint64))
+
+
+def contains_all(pairs, wanted):
+    """Every pair of `wanted` is among `pairs` (vectorised; no Python sets)."""
+    k, w = pair_keys(pairs), pair_keys(wanted)
+    if len(w) == 0:
+        return True
+    if len(k) == 0:
+        return False
+    i = np.minimum(np.searchsorted(k, w), len(k) - 1)
+    return bool(np.all(k[i] == w))
+
+
 def gpu_pairs(inst, **kw):
     rec = gpu_records(inst, **kw)
     codes = kw.get("codes", inst.codes)

@@ -124,3 +124,55 @@ def test_larger_database_reduce_is_exact():
         _check(ctx, ora)
         codes = inst.codes[:256]
         assert np.array_equal(gss.expand_reports(ctx.run(codes)), ora.pairs(codes))
+
+
+@pytest.mark.parametrize("layout", [gss.GSS_LAYOUT_IDENTITY, gss.GSS_LAYOUT_FREQUENCY])
+def test_export_rebuilds_the_database(layout):
+    """The export gives the resident clauses in the caller's numbering (the frequency layout's
+    renaming undone) with their ids; a context built from it reports the same pairs."""
+    n_vars = 400
+    ora = ActivityOracle(0.9)
+    off, lits = _db(n_vars, 3000, 61)
+    with gss.Context(n_vars, layout=layout, report_capacity=1 << 20, max_assignments=64) as ctx:
+        ctx.set_activity(0.9)
+        ctx.add_clauses(off, lits)
+        ora.add(off, lits)
+        e_off, e_lits, e_ids = ctx.export_clauses()
+        assert np.array_equal(e_off, off) and np.array_equal(e_lits, lits)
+        assert np.array_equal(e_ids, np.arange(len(off) - 1, dtype=np.uint32))
+        for step in range(3):
+            codes = _codes(n_vars, 64, 500 + step)
+            ora.after_test(gss.expand_reports(ctx.run(codes))[:, 0])
+        ctx.reduce_db(0.5)
+        ora.reduce(0.5)
+        e_off, e_lits, e_ids = ctx.export_clauses()
+        assert np.array_equal(e_off, ora.offsets) and np.array_equal(e_lits, ora.lits)
+        assert np.array_equal(e_ids, ora.ids)
+        codes = _codes(n_vars, 64, 600)
+        want = gss.expand_reports(ctx.run(codes))
+    with gss.Context(n_vars, layout=layout, report_capacity=1 << 20, max_assignments=64) as ctx2:
+        ctx2.add_clauses(e_off, e_lits)
+        got = gss.expand_reports(ctx2.run(codes))
+    got[:, 0] = e_ids[got[:, 0]]  # the rebuilt context numbers clauses from 0
+    order = np.lexsort((got[:, 1], got[:, 0]))
+    assert np.array_equal(got[order], want)
+
+
+def test_record_and_overflow_counters():
+    import ctypes
+    inst = synth.tiny()
+    with gss.Context(inst.n_vars, report_capacity=100, max_assignments=64) as ctx:
+        ctx.add_clauses(inst.offsets, inst.lits)
+        ctx.set_assignments(inst.codes)
+        ctx.test()
+        cnt = ctypes.c_uint64()
+        for _ in range(2):  # reading twice counts once
+            assert gss.load().gss_report_count(ctx.ptr, ctypes.byref(cnt)) == gss.GSS_E_OVERFLOW
+        n = cnt.value
+        st = ctx.stats()
+        assert n > 100 and st["records"] == n and st["overflows"] == 1
+        ctx.set_report_capacity(n)
+        ctx.test()
+        assert ctx.report_count() == n
+        st = ctx.stats()
+        assert st["records"] == 2 * n and st["overflows"] == 1

@@ -5,7 +5,7 @@ import pytest
 import oracle
 import paper_2012_03119_gb300 as gss
 import synth
-from gpu_util import check_records
+from gpu_util import check_records, contains_all
 
 pytestmark = pytest.mark.gpu
 
@@ -20,8 +20,7 @@ def test_single_instance_full_size():
     got = gss.expand_reports(rec)
     want = oracle.allf_pairs(inst.offsets, inst.lits, inst.codes)
     assert got.shape == want.shape and np.array_equal(got, want)
-    s = set(map(tuple, got.tolist()))
-    assert all(tuple(p) in s for p in inst.planted.tolist())
+    assert contains_all(got, inst.planted)
 
 
 def test_structured_full_size_sampled():
@@ -33,8 +32,7 @@ def test_structured_full_size_sampled():
         rec = ctx.run(inst.codes)
     check_records(rec, inst.n_clauses, inst.n_assign)
     got = gss.expand_reports(rec)
-    s = set(map(tuple, got.tolist()))
-    assert all(tuple(p) in s for p in inst.planted.tolist())
+    assert contains_all(got, inst.planted)
     lo, hi = 480, 544  # two whole 32-assignment groups
     want = oracle.allf_pairs(inst.offsets, inst.lits, inst.codes, a_range=(lo, hi))
     sub = got[(got[:, 1] >= lo) & (got[:, 1] < hi)]
@@ -60,8 +58,7 @@ def test_batch_full_size():
     by_size = sorted(range(len(insts)), key=lambda i: insts[i].n_clauses * insts[i].n_assign)
     full = set(by_size[:: max(1, len(by_size) // 14)]) | {by_size[0], by_size[-1]}
     for i, (I, g) in enumerate(zip(insts, got)):
-        s = set(map(tuple, g.tolist()))
-        assert all(tuple(p) in s for p in I.planted.tolist()), I.name
+        assert contains_all(g, I.planted), I.name
         assert len(g) == 0 or (g[:, 0].max() < I.n_clauses and g[:, 1].max() < I.n_assign)
         if i in full:
             want = oracle.allf_pairs(I.offsets, I.lits, I.codes)

@@ -216,3 +216,22 @@ def test_serve_identity_layout(work, snaps):
         srv.add_clauses(*work.csr(0, work.n_initial))
         pairs, _ = run_alone(srv, snaps[3])
         np.testing.assert_array_equal(pairs, prefix_oracle(work, work.n_initial, snaps[3]))
+
+
+def test_serve_result_deadline(work, snaps):
+    """A client that never collects its kept results (a solver thread that died): they are
+    dropped after result_ttl_us and counted; a waiting client is never cut off."""
+    with make_server(work, result_ttl_us=200_000) as srv:
+        srv.add_clauses(*work.csr(0, work.n_initial))
+        lost = srv.submit(snaps[0], wait_us=10_000_000)
+        rec, _ = srv.wait(srv.submit(snaps[1], wait_us=10_000_000))  # taken in time
+        deadline = time.time() + 10
+        while srv.stats()["expired"] == 0 and time.time() < deadline:
+            time.sleep(0.05)
+        assert srv.stats()["expired"] == 1
+        with pytest.raises(gss.GssError) as ei:
+            srv.wait(lost)
+        assert ei.value.code == gss.GSS_E_INVAL
+        # a result taken within the deadline is unaffected
+        rec, info = srv.wait(srv.submit(snaps[2], wait_us=10_000_000), wait_us=5_000_000)
+        np.testing.assert_array_equal(gss.expand_reports(rec), prefix_oracle(work, work.n_initial, snaps[2]))
