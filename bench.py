@@ -462,6 +462,8 @@ def main():
     ap.add_argument("--serve-threads", type=int, default=32)
     ap.add_argument("--serve-sat-requests", type=int, default=1024)
     ap.add_argument("--serve-tests-in-flight", type=int, default=1)
+    ap.add_argument("--mode", default="allf", choices=["allf", "trigger"],
+                    help="what a pair reports: all literals F (default) or Definition 'triggers'")
     ap.add_argument("--layout", default="frequency", choices=["frequency", "identity"],
                     help="internal variable numbering of the clause database")
     args = ap.parse_args()
@@ -499,9 +501,11 @@ def main():
     inst, workload = make_instance(args.config, rank, args.scale)
     stream = torch.cuda.Stream()
     N, V, m = inst.n_assign, inst.n_vars, inst.n_clauses
-    cap = max(1 << 22, 8 * len(inst.planted) + 4 * m)
+    cap = max(1 << 22, 8 * len(inst.planted) + (16 if args.mode == "trigger" else 4) * m)
     layout = gss.GSS_LAYOUT_FREQUENCY if args.layout == "frequency" else gss.GSS_LAYOUT_IDENTITY
-    ctx = gss.Context(V, device=local, stream=stream, report_capacity=cap, max_assignments=max(N, 32), layout=layout)
+    mode = gss.GSS_MODE_TRIGGER if args.mode == "trigger" else gss.GSS_MODE_ALLF
+    ctx = gss.Context(V, device=local, stream=stream, report_capacity=cap, max_assignments=max(N, 32), layout=layout,
+                      mode=mode)
 
     # a-1: ingest the database (once; the database stays resident like the paper's GPU clause store)
     torch.cuda.synchronize()
@@ -602,7 +606,7 @@ def main():
                    "seed": inst.params.get("seed"), "l2": "inputs larger than L2 (1 GB codes + 0.26 GB planes "
                    "streamed per step)" if args.config == "single" and args.scale == 1.0 else "see sizes",
                    "parallelism": f"weak x{world}: one clause database per GPU, shared assignment set",
-                   "layout": args.layout},
+                   "layout": args.layout, "mode": args.mode},
         "e2e": {"value": whole_job_rate(m * N, world, e2e_steps, e2e_s), "unit": UNIT, "h2d_bytes_per_step": N * V,
                 "d2h_bytes_per_step": 12 * n_records + 48},
         "roofline": {k: v for k, v in roof[dominant].items()},
