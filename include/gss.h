@@ -230,7 +230,9 @@ typedef struct {
   uint32_t grid[3];            /* autotuned CTAs, per group */
   uint64_t n_tiles[3];         /* 32-clause tiles per group */
   uint64_t runs;               /* gss_batch_test calls */
-  float tuned_test_us;         /* test-launch time measured by the autotuner */
+  float tuned_test_us;         /* test-launch time measured by the autotuner (0 when the choices came
+                                  from the cache file named by the environment variable
+                                  GSS_AUTOTUNE_CACHE, which keeps them across processes) */
 } gss_batch_info;
 
 /* Create an empty batch (cfg: device, stream, mode, layout; the rest is per instance). */

@@ -14,8 +14,13 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
 #include <new>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -183,9 +188,54 @@ int enqueue_packs(gss_batch* b) {  // on the side streams, forked from and joine
   return GSS_OK;
 }
 
+// Tuned choices can persist across processes: with GSS_AUTOTUNE_CACHE naming a file, each
+// group's (tiles per steal, grid) is stored under a key of the device, the mode, the row
+// width and the octave of the group's tile count, and reused by later runs.
+std::mutex g_cache_mutex;
+
+std::string cache_key(const gss_batch* b, const Group& g) {
+  cudaDeviceProp p{};
+  cudaGetDeviceProperties(&p, b->device);
+  uint32_t oct = 0;
+  while ((g.n_tiles >> oct) > 1) ++oct;
+  std::ostringstream k;
+  for (const char* c = p.name; *c; ++c) k << (*c == ' ' ? '_' : *c);
+  k << "/sm" << b->n_sms << "/mode" << b->mode << "/awp" << g.awp << "/oct" << oct;
+  return k.str();
+}
+
+std::map<std::string, std::pair<uint32_t, int>> read_cache(const char* path) {
+  std::map<std::string, std::pair<uint32_t, int>> m;
+  std::ifstream f(path);
+  std::string key;
+  uint32_t grab;
+  int grid;
+  while (f >> key >> grab >> grid)
+    if (grab >= 1 && grab <= 64 && grid >= 1) m[key] = {grab, grid};
+  return m;
+}
+
 // Time (tiles per steal, grid) candidates for each group's test launch; keep the fastest.
 int autotune(gss_batch* b) {
   int rc;
+  const char* cache_path = getenv("GSS_AUTOTUNE_CACHE");
+  std::map<std::string, std::pair<uint32_t, int>> cache;
+  if (cache_path && *cache_path) {
+    std::lock_guard<std::mutex> lk(g_cache_mutex);
+    cache = read_cache(cache_path);
+  }
+  bool all_cached = !cache.empty();
+  for (const Group& g : b->groups) all_cached = all_cached && cache.count(cache_key(b, g)) > 0;
+  if (all_cached) {  // earlier runs tuned every group of this shape
+    for (Group& g : b->groups) {
+      const auto& v = cache[cache_key(b, g)];
+      g.grab = v.first;
+      g.grid = v.second < g.grid ? v.second : g.grid;
+    }
+    b->tuned_us = 0.f;
+    b->tuned = true;
+    return GSS_OK;
+  }
   if ((rc = enqueue_resets(b, b->stream)) || (rc = enqueue_packs(b))) return rc;
   cudaEvent_t e0, e1;
   BCK(b, cudaEventCreate(&e0));
@@ -226,6 +276,11 @@ int autotune(gss_batch* b) {
   cudaEventDestroy(e1);
   b->tuned_us = total * 1e3f;
   b->tuned = true;
+  if (cache_path && *cache_path) {  // append this batch's choices (a later line wins on reading)
+    std::lock_guard<std::mutex> lk(g_cache_mutex);
+    std::ofstream f(cache_path, std::ios::app);
+    for (const Group& g : b->groups) f << cache_key(b, g) << ' ' << g.grab << ' ' << g.grid << '\n';
+  }
   return GSS_OK;
 }
 

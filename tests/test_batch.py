@@ -101,3 +101,40 @@ def test_empty_instances_and_state_errors():
         b.test()
         check_all(b, insts)
         assert len(b.fetch_reports(i)) == 0 and len(b.fetch_reports(j)) == 0
+
+
+def test_autotune_cache_file(tmp_path):
+    """With GSS_AUTOTUNE_CACHE set, the first process tunes and writes its choices; the second
+    takes them from the file (no timing) and gives the same records."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = r"""
+import json, sys
+sys.path.insert(0, sys.argv[1])
+import numpy as np, oracle, synth
+import paper_2012_03119_gb300 as gss
+insts = [synth.batch_instance(s) for s in synth.batch_specs(5, scale=0.01, seed=77)]
+with gss.Batch() as b:
+    for I in insts:
+        b.set_assignments(b.add_instance(I.n_vars, I.offsets, I.lits, max_assignments=I.n_assign,
+                                         report_capacity=1 << 20), I.codes)
+    b.test()
+    same = all(np.array_equal(gss.expand_reports(b.fetch_reports(i)), oracle.allf_pairs(I.offsets, I.lits, I.codes))
+               for i, I in enumerate(insts))
+    info = b.info()
+print(json.dumps({"same": same, "tuned_us": info["tuned_test_us"], "grab": info["tiles_per_steal"]}))
+"""
+    cache = tmp_path / "tune.txt"
+    env = dict(os.environ, GSS_AUTOTUNE_CACHE=str(cache))
+    runs = []
+    for _ in range(2):
+        r = subprocess.run([sys.executable, "-c", script, root], env=env, capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0, r.stderr[-2000:]
+        runs.append(json.loads(r.stdout.strip().splitlines()[-1]))
+    assert runs[0]["same"] and runs[1]["same"]
+    assert runs[0]["tuned_us"] > 0 and runs[1]["tuned_us"] == 0
+    assert runs[1]["grab"] == runs[0]["grab"]
+    assert len(cache.read_text().split("\n")) >= 2
