@@ -267,6 +267,7 @@ int gss_batch_test(gss_batch* b);
 int gss_batch_report_count(gss_batch* b, uint32_t instance, uint64_t* n_out);
 int gss_batch_fetch_reports(gss_batch* b, uint32_t instance, gss_report* out, uint64_t cap, uint64_t* n_out);
 
+/* The batch's launch groups and the autotuner's choices (GSS_E_INVAL for NULL arguments). */
 int gss_batch_get_info(const gss_batch* b, gss_batch_info* out);
 const char* gss_batch_last_error(const gss_batch* b);
 
@@ -434,6 +435,8 @@ typedef struct {
   double p50_us, p99_us, max_us, mean_us; /* latency of completed requests */
 } gss_server_stats;
 
+/* Fill *cfg with the defaults: device 0, all-F, frequency layout, 1M clauses and 16M literals
+ * reserved, 64 slots, 3 lanes, one test in flight, 1M records per lane, results kept forever. */
 int gss_server_config_init(gss_server_config* cfg);
 
 /* Create a server for n_vars variables; reserves the database and request slots and starts
@@ -471,6 +474,7 @@ int gss_server_submit(gss_server* srv, const uint8_t* values, uint32_t n_assign,
 int gss_server_wait(gss_server* srv, uint64_t request_id, int64_t wait_us, gss_report* out, uint64_t cap,
                     uint64_t* n_out, gss_request_info* info);
 
+/* Counters since creation and the latency percentiles of every completed request. */
 int gss_server_get_stats(gss_server* srv, gss_server_stats* out);
 const char* gss_server_last_error(const gss_server* srv);
 
@@ -486,6 +490,7 @@ const char* gss_server_last_error(const gss_server* srv);
  */
 int gss_debug_bounds(uint32_t* enabled, uint64_t* errors, int reset);
 
+/* Sizes, counters and the last test's aggregate-test counts (see gss_stats). */
 int gss_get_stats(const gss_ctx* ctx, gss_stats* out);
 
 /* Message of the last failed call on ctx ("" if none); a static string for NULL ctx. */
