@@ -114,7 +114,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_instance(config: str, rank: int, scale: float):
+def make_instance(config: str, rank: int, scale: float, n_assign: int = 8192):
     import synth
     if config == "single":
         inst = synth.single(scale=scale, seed=synth.seed_for(2, rank))
@@ -127,6 +127,12 @@ def make_instance(config: str, rank: int, scale: float):
             f"1024 trail assignments (scaled x{scale:g})")
     if config == "tiny":
         return synth.tiny(), "plain test, tiny: 2,000 vars, 20,000 clauses, 64 assignments"
+    if config == "wide":
+        inst = synth.wide(scale=scale, seed=synth.seed_for(6, rank), n_assign=n_assign)
+        if rank:
+            inst.codes = synth.wide(scale=scale, seed=synth.seed_for(6, 0), n_assign=n_assign).codes
+        return inst, (f"wide set: 1M vars, 4M clauses (lognormal sizes median 20), {n_assign} trail assignments in "
+                      f"groups of 1024; two aggregate levels" + ("" if scale == 1.0 else f" (scaled x{scale:g})"))
     raise SystemExit(f"unknown config {config}")
 
 
@@ -152,6 +158,44 @@ def algorithmic_bytes(inst, n_records: int) -> dict:
     m, L, V, N = inst.n_clauses, inst.n_lits, inst.n_vars, inst.n_assign
     W = (N + 31) // 32
     return {"test": 4 * (m + 1) + 4 * L + 2 * V * W * 4 + 12 * n_records, "pack": N * V + 2 * V * W * 4}
+
+
+def narrow_split(gss, ctx, stream, d_codes, pitch, N, m, wide_pairs, steps):
+    """The same N assignments as sets of at most 4096 (no level-2 filter), through the same
+    context: the records must be the wide test's, and the time is what the wide path saves."""
+    import torch
+    n_max = gss.GSS_MAX_NARROW_ASSIGNMENTS
+    chunks = [(a, min(N, a + n_max)) for a in range(0, N, n_max)]
+
+    def run(collect):
+        got = []
+        for a, b in chunks:
+            gss.gss_set_assignments_device(ctx.ptr, d_codes.data_ptr() + a * pitch, pitch, b - a)
+            ctx.test()
+            if collect:
+                p = gss.expand_reports(ctx.fetch_reports())
+                p[:, 1] += a
+                got.append(p)
+            else:
+                ctx.report_count()
+        return got
+
+    got = np.concatenate(run(True))
+    got = got[np.lexsort((got[:, 1], got[:, 0]))]
+    same = bool(np.array_equal(got, wide_pairs))
+    for _ in range(2):
+        run(False)
+    k = max(3, min(steps, 10))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(k):
+        run(False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / k
+    return {"chunks": len(chunks), "ms_per_step": t * 1e3, "tests_per_s_G": m * N / t / 1e9,
+            "identical_pairs": same}
 
 
 def cpu_baseline(inst, max_seconds: float = 15.0) -> dict:
@@ -453,7 +497,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gss", choices=["gss", "reference"])
-    ap.add_argument("--config", default="single", choices=["single", "structured", "tiny", "batch", "serve"])
+    ap.add_argument("--config", default="single", choices=["single", "structured", "tiny", "wide", "batch", "serve"])
+    ap.add_argument("--n-assign", type=int, default=8192, help="assignments of the wide workload (<= 32768)")
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--ref-assignments", type=int, default=64)
@@ -484,7 +529,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        inst, workload = make_instance(args.config, 0, args.scale)
+        inst, workload = make_instance(args.config, 0, args.scale, args.n_assign)
         print(json.dumps(run_reference(args, inst, workload)), flush=True)
         return
 
@@ -498,10 +543,10 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     warmup = max(3, args.warmup)
-    inst, workload = make_instance(args.config, rank, args.scale)
+    inst, workload = make_instance(args.config, rank, args.scale, args.n_assign)
     stream = torch.cuda.Stream()
     N, V, m = inst.n_assign, inst.n_vars, inst.n_clauses
-    cap = max(1 << 22, 8 * len(inst.planted) + (16 if args.mode == "trigger" else 4) * m)
+    cap = max(1 << 22, 8 * len(inst.planted) + (16 if args.mode == "trigger" else 4) * m * ((N + 1023) // 1024))
     layout = gss.GSS_LAYOUT_FREQUENCY if args.layout == "frequency" else gss.GSS_LAYOUT_IDENTITY
     mode = gss.GSS_MODE_TRIGGER if args.mode == "trigger" else gss.GSS_MODE_ALLF
     ctx = gss.Context(V, device=local, stream=stream, report_capacity=cap, max_assignments=max(N, 32), layout=layout,
@@ -533,6 +578,10 @@ def main():
     aggregate = {"candidate_pairs": st["candidate_pairs"], "group_pairs": st["group_pairs"],
                  "negative_ratio": 1.0 - st["candidate_pairs"] / max(1, st["group_pairs"]),
                  "paper_negative_ratio": 0.999422}
+    if N > gss.GSS_MAX_NARROW_ASSIGNMENTS:  # the level-2 (1024-assignment) filter in front of it
+        sg = m * ((N + 1023) // 1024)
+        aggregate.update({"super_pairs": st["super_pairs"], "super_group_pairs": sg,
+                          "super_negative_ratio": 1.0 - st["super_pairs"] / max(1, sg)})
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -563,6 +612,10 @@ def main():
     t_test = float(np.mean([e[1].elapsed_time(e[2]) for e in ev])) / 1e3
     elapsed = max_over_ranks(elapsed, dist)
 
+    split = None
+    if N > gss.GSS_MAX_NARROW_ASSIGNMENTS:
+        split = narrow_split(gss, ctx, stream, d_codes, pitch, N, m, pairs, args.steps)
+
     # e2e through the public API from pinned host memory
     e2e_steps = args.e2e_steps or max(3, min(args.steps, 20))
     h_codes = torch.empty((N, V), dtype=torch.uint8).pin_memory()
@@ -587,14 +640,17 @@ def main():
     value = whole_job_rate(m * N, world, args.steps, elapsed)
     pk = peaks()
     B = algorithmic_bytes(inst, n_records)
+    single = args.config == "single" and args.scale == 1.0
     roof = {
         "pack": {"bound": "hbm", "achieved": B["pack"] / t_pack / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
                  "frac": B["pack"] / t_pack / 1e9 / pk["hbm_gbs"], "time_us": t_pack * 1e6, "bytes": B["pack"],
-                 "traffic": profiled_traffic("k_pack.cu", "k_pack__single_V1M_N1024.md"), "kernel": "k_pack",
+                 "traffic": profiled_traffic("k_pack.cu", "k_pack__single_V1M_N1024.md") if single else None,
+                 "kernel": "k_pack",
                  "peak_source": f"{pk['source']} hbm_gbs"},
         "test": {"bound": "hbm", "achieved": B["test"] / t_test / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
                  "frac": B["test"] / t_test / 1e9 / pk["hbm_gbs"], "time_us": t_test * 1e6, "bytes": B["test"],
-                 "traffic": profiled_traffic("k_test.cu", "k_test__single_V1M_N1024.md"), "kernel": "k_test",
+                 "traffic": profiled_traffic("k_test.cu", "k_test__single_V1M_N1024.md") if single else None,
+                 "kernel": "k_test",
                  "peak_source": f"{pk['source']} hbm_gbs"},
     }
     dominant = "pack" if t_pack >= t_test else "test"
@@ -603,8 +659,9 @@ def main():
         "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": workload, "n_vars": V, "n_clauses": m, "n_lits": inst.n_lits, "n_assign": N,
-                   "seed": inst.params.get("seed"), "l2": "inputs larger than L2 (1 GB codes + 0.26 GB planes "
-                   "streamed per step)" if args.config == "single" and args.scale == 1.0 else "see sizes",
+                   "seed": inst.params.get("seed"),
+                   "l2": f"inputs larger than L2 ({N * V / 1e9:.3g} GB codes + {8 * V * ((N + 31) // 32) / 1e9:.3g} GB "
+                         "planes streamed per step)" if N * V > 129e6 else "inputs smaller than L2",
                    "parallelism": f"weak x{world}: one clause database per GPU, shared assignment set",
                    "layout": args.layout, "mode": args.mode},
         "e2e": {"value": whole_job_rate(m * N, world, e2e_steps, e2e_s), "unit": UNIT, "h2d_bytes_per_step": N * V,
@@ -620,6 +677,8 @@ def main():
         "aggregate_test": aggregate,
         "clocks": clk,
     }
+    if split:
+        out["narrow_split"] = split
     ctx.close()
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(inst)

@@ -62,7 +62,15 @@ enum { GSS_MODE_ALLF = 0, GSS_MODE_TRIGGER = 1 };
  */
 enum { GSS_LAYOUT_IDENTITY = 0, GSS_LAYOUT_FREQUENCY = 1 };
 
-#define GSS_MAX_ASSIGNMENTS 4096u /* largest N per assignment set */
+/*
+ * Largest N per assignment set.  Sets of more than GSS_MAX_NARROW_ASSIGNMENTS are tested
+ * with a second aggregate level (Section 7's aggregate of aggregates): one bit per
+ * 1024-assignment super-group per literal filters (clause, super-group) pairs before the
+ * 32-assignment groups of Section 4.2 do; results are the same.  Batches
+ * (gss_batch_*) and gss_test_noalloc take at most GSS_MAX_NARROW_ASSIGNMENTS.
+ */
+#define GSS_MAX_ASSIGNMENTS 32768u
+#define GSS_MAX_NARROW_ASSIGNMENTS 4096u
 #define GSS_HEAD_WIDTH 16u        /* literals per clause kept in the head planes */
 
 typedef struct gss_ctx gss_ctx;
@@ -107,6 +115,9 @@ typedef struct {
   uint64_t next_clause_id;  /* id the next added clause gets (ids are never reused) */
   uint64_t records;         /* records produced by the tests whose results were read, in total */
   uint64_t overflows;       /* of those tests, how many produced more records than the capacity */
+  uint64_t super_pairs;     /* last test, sets of more than GSS_MAX_NARROW_ASSIGNMENTS only:
+                               (clause, 1024-assignment super-group) pairs whose level-2 aggregate
+                               test was positive; 0 otherwise */
 } gss_stats;
 
 /* ------------------------------------------------------------ lifecycle */
@@ -245,7 +256,8 @@ int gss_batch_destroy(gss_batch* b);
  * Add an instance of n_vars variables holding the given clauses (as
  * gss_add_clauses), able to take up to max_assignments assignments and to hold
  * report_capacity records (0: the defaults of gss_config_init).  *instance_id
- * receives its index (dense, from 0).  Synchronises the stream.
+ * receives its index (dense, from 0).  max_assignments <= GSS_MAX_NARROW_ASSIGNMENTS
+ * (GSS_E_INVAL otherwise).  Synchronises the stream.
  */
 int gss_batch_add_instance(gss_batch* b, uint32_t n_vars, uint32_t max_assignments, uint64_t report_capacity,
                            const uint64_t* offsets, uint64_t n_clauses, const uint32_t* lits,
@@ -338,7 +350,8 @@ int gss_export_clauses(gss_ctx* ctx, uint64_t* offsets, uint64_t cap_clauses, ui
  *   d_offsets, n_clauses, d_lits  the clauses, as gss_add_clauses but in device memory
  *   n_vars                        V (literals 2v + s < 2V)
  *   d_values, pitch, n_assign     value codes as gss_set_assignments_device; here the
- *                                 pointer and pitch must be multiples of 16
+ *                                 pointer and pitch must be multiples of 16 and
+ *                                 n_assign <= GSS_MAX_NARROW_ASSIGNMENTS
  *   mode                          GSS_MODE_ALLF or GSS_MODE_TRIGGER
  *   d_out, cap                    record buffer (gss_report, record order unspecified)
  *   d_count                       device counter that receives the number of records
@@ -476,6 +489,7 @@ int gss_server_wait(gss_server* srv, uint64_t request_id, int64_t wait_us, gss_r
 
 /* Counters since creation and the latency percentiles of every completed request. */
 int gss_server_get_stats(gss_server* srv, gss_server_stats* out);
+/* Message of the calling thread's last failed call on a server (each thread keeps its own). */
 const char* gss_server_last_error(const gss_server* srv);
 
 /* ---------------------------------------------------------- diagnostics */

@@ -24,7 +24,8 @@ GSS_OK, GSS_E_INVAL, GSS_E_NOMEM, GSS_E_CUDA, GSS_E_OVERFLOW, GSS_E_TIMEOUT, GSS
     0, -1, -2, -3, -4, -5, -6, -7
 GSS_MODE_ALLF, GSS_MODE_TRIGGER = 0, 1
 GSS_LAYOUT_IDENTITY, GSS_LAYOUT_FREQUENCY = 0, 1
-GSS_MAX_ASSIGNMENTS = 4096
+GSS_MAX_ASSIGNMENTS = 32768
+GSS_MAX_NARROW_ASSIGNMENTS = 4096
 GSS_SUBMIT_KEEP = 1
 GSS_WATERMARK_ALL = 0xFFFFFFFFFFFFFFFF
 GSS_HEAD_WIDTH = 16
@@ -44,7 +45,7 @@ class gss_stats(ctypes.Structure):
                 ("tests_run", ctypes.c_uint64), ("pair_tests", ctypes.c_uint64),
                 ("candidate_pairs", ctypes.c_uint64), ("group_pairs", ctypes.c_uint64),
                 ("clauses_removed", ctypes.c_uint64), ("next_clause_id", ctypes.c_uint64),
-                ("records", ctypes.c_uint64), ("overflows", ctypes.c_uint64)]
+                ("records", ctypes.c_uint64), ("overflows", ctypes.c_uint64), ("super_pairs", ctypes.c_uint64)]
 
 
 class gss_batch_info(ctypes.Structure):

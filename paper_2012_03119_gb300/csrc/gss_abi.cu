@@ -121,7 +121,7 @@ uint32_t words_stride(uint32_t N) {  // plane row stride in 32-bit words: a powe
   return p;
 }
 
-uint32_t agg_stride(uint32_t Wp) { return Wp <= 32 ? 1 : Wp / 32; }  // 1, 2 or 4 words
+uint32_t agg_stride(uint32_t Wp) { return Wp <= 32 ? 1 : Wp / 32; }  // 1, 2, 4, ... 32 words
 
 int ensure_planes(gss_ctx* c) {  // allocates what is missing, so a call after a failed one completes the set
   const uint32_t Wp = words_stride(c->max_N), AWp = agg_stride(Wp);
@@ -139,6 +139,14 @@ int ensure_planes(gss_ctx* c) {  // allocates what is missing, so a call after a
     if ((rc = dev_alloc(c, &p, (c->V + 1ull) * AWp * 4))) return rc;
     c->aggU = static_cast<uint32_t*>(p);
   }
+  if (AWp > 4 && !c->agg2F) {
+    if ((rc = dev_alloc(c, &p, (2ull * c->V + 2) * 4))) return rc;
+    c->agg2F = static_cast<uint32_t*>(p);
+  }
+  if (AWp > 4 && !c->agg2U) {
+    if ((rc = dev_alloc(c, &p, (c->V + 1ull) * 4))) return rc;
+    c->agg2U = static_cast<uint32_t*>(p);
+  }
   return GSS_OK;
 }
 
@@ -149,8 +157,9 @@ int sync_status(gss_ctx* c) {
 }
 
 int launch_grid(gss_ctx* c, int mode, uint32_t AWp) {
-  int& g = c->grid[mode][AWp];
-  if (!g) g = test_grid_size(mode, AWp, c->n_sms);
+  const bool wide = AWp > 4;
+  int& g = wide ? c->grid_wide[mode] : c->grid[mode][AWp];
+  if (!g) g = test_grid_size(mode, AWp, c->n_sms, wide);
   return g;
 }
 
@@ -375,6 +384,7 @@ int stage_assignments(gss_ctx* c, const uint8_t* src, uint64_t pitch, uint32_t n
 int pack_staged(gss_ctx* c, cudaStream_t s) {
   if (c->N) CK(c, launch_pack(c->pack_src, c->pack_pitch, c->V, c->N, c->Wp, c->AWp, c->map, c->P, c->aggF, c->aggU,
                               c->st, s));
+  if (c->N && c->AWp > 4) CK(c, launch_agg2(c->aggF, c->aggU, c->V, c->AWp, c->agg2F, c->agg2U, s));
   return GSS_OK;
 }
 }  // namespace host
@@ -405,13 +415,19 @@ int gss_test(gss_ctx* c) {
   if (!c->have_assign) return fail(c, GSS_E_STATE, "gss_test before gss_set_assignments");
   DeviceGuard dg(c->device);
   CK(c, cudaMemsetAsync(&c->st->n_records, 0, 2 * sizeof(unsigned long long), c->stream));  // records, candidates
+  CK(c, cudaMemsetAsync(&c->st->n_super, 0, sizeof(unsigned long long), c->stream));
   if (c->m && c->N) {
     ClauseView db{c->off, c->lits, c->head0, c->head1, 2u * c->V, c->ext};
     PlaneView pv{c->P, c->aggF, c->aggU, c->Wp, c->AWp, c->N, c->V};
+    WideView wv;
+    if (c->AWp > 4) {  // stage A on the level-2 rows, the level-1 rows in stage B
+      pv = PlaneView{c->P, c->agg2F, c->agg2U, c->Wp, 1u, c->N, c->V};
+      wv = WideView{c->aggF, c->aggU, c->AWp};
+    }
     ActivityView av;
     if (c->act) av = ActivityView{c->act, c->stamp, c->epoch, c->inc};
     CK(c, launch_test((int)c->mode, db, 0, c->m, pv, c->rec, c->rec_cap, c->st, launch_grid(c, c->mode, c->AWp),
-                      c->stream, nullptr, 0, av));
+                      c->stream, nullptr, 0, av, wv));
   }
   if (c->act) {  // after the test's bumps: the increment grows by 1 / decay, rescaled past 1e20
     c->epoch = c->epoch + 1 == 0xFFFFFFFFu ? 0 : c->epoch + 1;
@@ -549,6 +565,7 @@ int gss_get_stats(const gss_ctx* c, gss_stats* o) {
   o->tests_run = c->tests_run;
   o->pair_tests = c->pair_tests;
   o->candidate_pairs = c->tested ? c->h_st[0].n_candidates : 0;
+  o->super_pairs = c->tested ? c->h_st[0].n_super : 0;
   o->clauses_removed = c->removed;
   o->records = c->records;
   o->overflows = c->overflows;

@@ -391,6 +391,9 @@ int gss_batch_add_instance(gss_batch* b, uint32_t n_vars, uint32_t max_assignmen
   cfg.mode = b->mode;
   cfg.layout = b->layout;
   if (max_assignments) cfg.max_assignments = max_assignments;
+  if (cfg.max_assignments > GSS_MAX_NARROW_ASSIGNMENTS)  // the batched kernel has no second aggregate level
+    return bfail(b, GSS_E_INVAL, "max_assignments %u > %u for a batch instance", max_assignments,
+                 GSS_MAX_NARROW_ASSIGNMENTS);
   if (report_capacity) cfg.report_capacity = report_capacity;
   gss_ctx* c = nullptr;
   int rc = gss_create(&c, n_vars, &cfg);

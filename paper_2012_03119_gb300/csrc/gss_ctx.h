@@ -48,6 +48,8 @@ struct gss_ctx {
   uint32_t* P = nullptr;
   uint32_t* aggF = nullptr;
   uint32_t* aggU = nullptr;
+  uint32_t* agg2F = nullptr;  // level-2 rows, held when max_N > GSS_MAX_NARROW_ASSIGNMENTS
+  uint32_t* agg2U = nullptr;
   const uint8_t* pack_src = nullptr;  // codes the next packing reads (staging buffer or caller memory)
   uint64_t pack_pitch = 0;
 
@@ -57,7 +59,8 @@ struct gss_ctx {
   DevStatus* st = nullptr;    // [0]: pack + test, [1]: ingest
   DevStatus* h_st = nullptr;  // pinned mirror
   bool tested = false;
-  int grid[2][5] = {{0}};     // cached persistent grid per (mode, AWp)
+  int grid[2][5] = {{0}};     // cached persistent grid per (mode, AWp <= 4)
+  int grid_wide[2] = {0, 0};  // per mode, for sets of more than GSS_MAX_NARROW_ASSIGNMENTS
 
   uint64_t tests_run = 0, pair_tests = 0;
   uint64_t records = 0, overflows = 0;  // of tests whose status was read

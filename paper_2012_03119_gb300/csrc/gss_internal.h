@@ -13,8 +13,10 @@
 //   aggF   u32 [2V + 2][AWp]     group aggregate of P: bit g set iff P[l][g] != 0
 //                                ("F is in G(l)" for the 32-assignment group g, Section 4.2)
 //   aggU   u32 [V + 1][AWp]      bit g set iff some assignment of group g leaves v U (row V = 0)
+//   agg2F  u32 [2V + 2]          wide sets only (AWp > 4): bit s set iff aggF[l][s] != 0, i.e. F is
+//   agg2U  u32 [V + 1]           in G(l) for the 1024-assignment super-group s; agg2U likewise
 // W = ceil(N / 32) words, Wp = row stride (a power of two >= max(4, W)),
-// AWp = max(1, Wp / 32) (1, 2 or 4).
+// AWp = max(1, Wp / 32) (1, 2, 4, ... 32).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -34,6 +36,7 @@ struct DevStatus {
   unsigned int bad_lit;          // ingest saw a literal >= 2V
   unsigned int bad_size;         // ingest saw an empty clause or offsets beyond the batch
   unsigned int timeout;          // a bounded device wait gave up
+  unsigned long long n_super;    // wide sets: (clause, super-group) pairs that passed the level-2 test
 };
 
 // Planes of one assignment set.
@@ -44,6 +47,20 @@ struct PlaneView {
   uint32_t Wp, AWp, N;
   uint32_t V;  // rows: P and aggF 2V + 2, aggU V + 1
 };
+
+// Wide assignment sets (more than 4096 assignments; Section 7's aggregate of aggregates): the
+// test's stage A then filters on level-2 rows of one word per literal (bit s: some assignment
+// of super-group s -- 32 groups, 1024 assignments -- makes the literal F / leaves the variable
+// U), and each (clause, super-group) pair left is tested on its level-1 words (one bit per
+// 32-assignment group) before the exact test of each group left.
+struct WideView {
+  const uint32_t* aggF1 = nullptr;  // [2V + 2][AWp1] level-1 rows
+  const uint32_t* aggU1 = nullptr;  // [V + 1][AWp1]
+  uint32_t AWp1 = 0;
+};
+// agg2F[r] bit s = (aggF1[r][s] != 0) for r < 2V + 2; agg2U[v] bit s = (aggU1[v][s] != 0) for v <= V.
+cudaError_t launch_agg2(const uint32_t* aggF1, const uint32_t* aggU1, uint32_t V, uint32_t AWp1, uint32_t* agg2F,
+                        uint32_t* agg2U, cudaStream_t s);
 
 // Bounds-checked build (GSS_DEBUG_BOUNDS): the test kernels check every row they gather from
 // and count violations in a device counter, reading the neutral PAD row instead.
@@ -97,7 +114,8 @@ cudaError_t launch_build_heads(const uint64_t* boff, uint64_t n, uint64_t L0, ui
 // entries, non-decreasing), clause c is tested against plane word w only if c < wm[w].
 cudaError_t launch_test(int mode, const ClauseView& db, uint64_t c_lo, uint64_t c_hi, const PlaneView& pv,
                         gss_report* rec, uint64_t cap, DevStatus* st, int grid, cudaStream_t s,
-                        const uint64_t* wm = nullptr, uint32_t n_wm = 0, const ActivityView& av = ActivityView{});
+                        const uint64_t* wm = nullptr, uint32_t n_wm = 0, const ActivityView& av = ActivityView{},
+                        const WideView& wide = WideView{});
 
 // Group a serving launch's records by plane word (request) into out: records of word w at
 // [sum of count[0..w), + count[w]), their mask ANDed with nmask[w], records left without a bit
@@ -132,7 +150,7 @@ cudaError_t launch_compact_copy(const uint64_t* off, const uint32_t* lits, const
                                 cudaStream_t s);
 
 // Occupancy-derived persistent grid for launch_test on this device.
-int test_grid_size(int mode, uint32_t AWp, int n_sms);
+int test_grid_size(int mode, uint32_t AWp, int n_sms, bool wide = false);
 
 // One instance of a batch as the batched test kernel sees it.
 struct BatchInst {

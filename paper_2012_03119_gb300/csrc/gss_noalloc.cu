@@ -65,7 +65,8 @@ extern "C" int gss_test_noalloc(const uint64_t* d_offsets, uint64_t n_clauses, c
   if (!d_count) return say(errbuf, errbuf_len, GSS_E_INVAL, "d_count is NULL");
   if (n_vars == 0 || n_vars >= (1u << 31)) return say(errbuf, errbuf_len, GSS_E_INVAL, "n_vars out of range");
   if (mode != GSS_MODE_ALLF && mode != GSS_MODE_TRIGGER) return say(errbuf, errbuf_len, GSS_E_INVAL, "unknown mode");
-  if (n_assign > GSS_MAX_ASSIGNMENTS) return say(errbuf, errbuf_len, GSS_E_INVAL, "n_assign > GSS_MAX_ASSIGNMENTS");
+  if (n_assign > GSS_MAX_NARROW_ASSIGNMENTS)
+    return say(errbuf, errbuf_len, GSS_E_INVAL, "n_assign > GSS_MAX_NARROW_ASSIGNMENTS");
   if (n_clauses >= (1ull << 32)) return say(errbuf, errbuf_len, GSS_E_INVAL, "more than 2^32 - 1 clauses");
   if (n_clauses && (!d_offsets || !d_lits)) return say(errbuf, errbuf_len, GSS_E_INVAL, "clause arrays are NULL");
   if (n_assign && !d_values) return say(errbuf, errbuf_len, GSS_E_INVAL, "d_values is NULL");

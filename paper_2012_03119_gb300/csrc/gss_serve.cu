@@ -128,11 +128,13 @@ struct gss_server {
   uint64_t submitted = 0, dropped = 0, completed = 0, launches = 0, words = 0, pair_tests = 0, reports = 0;
   uint64_t expired = 0;
   std::vector<double> lat_us;
-  std::mutex err_mu;
-  std::string err;
 };
 
 namespace {
+
+// The message of the calling thread's last failed server call: several threads use one
+// server at once, so each keeps its own.
+thread_local std::string t_err;
 
 int sfail(gss_server* v, int code, const char* fmt, ...) {
   char buf[512];
@@ -141,8 +143,7 @@ int sfail(gss_server* v, int code, const char* fmt, ...) {
   vsnprintf(buf, sizeof buf, fmt, ap);
   va_end(ap);
   if (v) {
-    std::lock_guard<std::mutex> g(v->err_mu);
-    v->err = buf;
+    t_err = buf;
   }
   return code;
 }
@@ -593,6 +594,6 @@ int gss_server_get_stats(gss_server* v, gss_server_stats* o) {
   return GSS_OK;
 }
 
-const char* gss_server_last_error(const gss_server* v) { return v ? v->err.c_str() : "no server"; }
+const char* gss_server_last_error(const gss_server* v) { return v ? t_err.c_str() : "no server"; }
 
 }  // extern "C"

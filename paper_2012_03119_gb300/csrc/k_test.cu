@@ -29,6 +29,12 @@
 //     atomicAdd and is written out as whole words.  Records past the capacity are counted
 //     but not written.
 //
+// Wide sets (more than 4096 assignments, the aggregate of aggregates that Section 7 proposes):
+// stage A runs on level-2 rows (one bit per 1024-assignment super-group), and each surviving
+// (clause, super-group) pair first runs the group recurrence on its level-1 word (one bit per
+// 32-assignment group of the super-group) before the exact test of each group left.  Both
+// aggregate levels are ORs of the level below, so the Theorem of Section 4.2 applies to each.
+//
 // The PAD literal 2V is neutral in both modes: its P and aggF rows are all ones and its
 // aggU row is zero, so padded head slots need no branch.
 //
@@ -36,6 +42,8 @@
 // the aggregate rows gathered most often share a few cache lines and stay in L1.  (A copy
 // of those rows in shared memory was measured: 182 us against 171 us without it on the
 // 4M-clause workload, so the L1 serves them better.)
+#include <type_traits>
+
 #include "gss_internal.h"
 #include "gss_ptx.h"
 
@@ -53,6 +61,10 @@ struct __align__(128) WarpSmem {
   uint32_t pairs[PAIR_CAP];  // owner lane | group << 5
   uint32_t out[3 * OUT_CAP]; // staged records {clause, word, mask}
   unsigned long long bar[2];
+};
+// Wide sets: pairs holds (clause, super-group) pairs, pairs2 the (clause, group) pairs of a round.
+struct __align__(128) WarpSmemWide : WarpSmem {
+  uint32_t pairs2[PAIR_CAP];
 };
 
 // ------------------------------------------------------------------ math helpers
@@ -183,6 +195,51 @@ __device__ __forceinline__ void exact_tail(const ClauseView& db, const PlaneView
   }
 }
 
+// Wide sets: the group recurrence of 8 literals on the level-1 word of super-group sg (bit b:
+// group 32 sg + b), gathers first.
+template <int MODE>
+__device__ __forceinline__ void group1_batch8(const WideView& wv, uint32_t V, const uint32_t (&l)[8], uint32_t sg,
+                                              uint32_t& af, uint32_t& ou) {
+  uint32_t cf[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) cf[j] = __ldg(wv.aggF1 + (uint64_t)GSS_ROW(l[j], 2u * V + 2u, 2u * V) * wv.AWp1 + sg);
+  if constexpr (MODE == GSS_MODE_ALLF) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) af &= cf[j];
+  } else {
+    uint32_t cu[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) cu[j] = __ldg(wv.aggU1 + (uint64_t)GSS_ROW(l[j] >> 1, V + 1u, V) * wv.AWp1 + sg);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      ou = (af & cu[j]) | (ou & cf[j]);
+      af &= cf[j];
+    }
+  }
+}
+
+// Groups of super-group sg whose level-1 aggregate test is positive for clause c (head0 in l0):
+// literals 8..15 from head1, then the CSR, while some group is alive.
+template <int MODE>
+__device__ __forceinline__ uint32_t group1_mask(const ClauseView& db, const PlaneView& pv, const WideView& wv,
+                                                const uint32_t (&l0)[8], uint64_t c, uint32_t sg) {
+  uint32_t af = FULL, ou = 0u;
+  group1_batch8<MODE>(wv, pv.V, l0, sg, af, ou);
+  if ((af | ou) != 0u && l0[7] != db.pad) {
+    uint32_t l[8];
+    load8_global(db.head1 + c * 8u, l);
+    group1_batch8<MODE>(wv, pv.V, l, sg, af, ou);
+    if ((af | ou) != 0u && l[7] != db.pad) {
+      const uint64_t e = db.off[c + 1];
+      for (uint64_t k0 = db.off[c] + HEAD_K; k0 < e && (af | ou) != 0u; k0 += 8) {
+        load8_csr(db.lits, k0, e, db.pad, l);
+        group1_batch8<MODE>(wv, pv.V, l, sg, af, ou);
+      }
+    }
+  }
+  return af | ou;
+}
+
 // Head0 of a staged pair: its owner lane's 8 literals in the warp's ring (PAD for no pair).
 __device__ __forceinline__ void pair_head(const uint32_t* __restrict__ h0, bool has, uint32_t pad, uint32_t (&l)[8]) {
   if (has) {
@@ -205,6 +262,8 @@ struct Outbox {
   unsigned long long* cand_cnt;  // candidate-pair counter of the same test
   uint32_t n;                    // staged records (warp-uniform)
   uint32_t cand;                 // candidate pairs counted by this lane, not yet added
+  unsigned long long* cand2_cnt = nullptr;  // wide sets: (clause, super-group) pairs past stage A
+  uint32_t cand2 = 0u;
 };
 static_assert(sizeof(gss_report) == 12, "gss_report is three 32-bit words");
 
@@ -230,6 +289,11 @@ __device__ __forceinline__ void out_close(Smem& S, Outbox& o, uint32_t lane) {
   const uint32_t c = __reduce_add_sync(FULL, o.cand);
   if (lane == 0 && c) atomicAdd(o.cand_cnt, (unsigned long long)c);
   o.cand = 0u;
+  if (o.cand2_cnt) {  // warp-uniform
+    const uint32_t c2 = __reduce_add_sync(FULL, o.cand2);
+    if (lane == 0 && c2) atomicAdd(o.cand2_cnt, (unsigned long long)c2);
+    o.cand2 = 0u;
+  }
 }
 
 template <typename Smem>
@@ -246,6 +310,46 @@ __device__ __forceinline__ void out_append(Smem& S, Outbox& o, bool has, uint32_
     S.out[j + 2] = mask;
   }
   o.n += k;
+}
+
+// Stage B proper: the exact recurrence of np staged pairs buf[0 .. np) (owner lane | group << 5,
+// the owner's head0 in ring), one pair per lane, records into the outbox.
+template <int MODE, bool EXTRA, typename Smem>
+__device__ __forceinline__ void exact_pairs(const ClauseView& db, const PlaneView& pv, Smem& S, const uint32_t* ring,
+                                            const uint32_t* buf, uint32_t np, uint64_t c0, uint32_t lane, Outbox& out,
+                                            const ActivityView& av) {
+  for (uint32_t p0 = 0; p0 < np; p0 += 32u) {
+    const uint32_t pa = p0 + lane;
+    const bool ha = pa < np;
+    const uint32_t ea = ha ? buf[pa] : 0u;
+    const uint32_t oa = ea & 31u, ga = ea >> 5;
+    uint32_t la[8];
+    pair_head(ring + oa * 8u, ha, db.pad, la);
+    const uint32_t va = valid_bits(pv.N, ga);
+    uint32_t afa = ha ? ((MODE == GSS_MODE_ALLF) ? FULL : va) : 0u, oua = 0u;
+    word_batch8<MODE>(pv, la, ga, va, afa, oua);
+    exact_tail<MODE>(db, pv, c0 + oa, ga, va, la[7], afa, oua);
+    const uint32_t ra = afa | oua;
+    const uint64_t cp = c0 + oa;  // position of the pair's clause
+    uint32_t id = (uint32_t)cp;
+    if constexpr (EXTRA) {
+      if (ra != 0u && av.act && atomicExch(av.stamp + cp, av.epoch) != av.epoch)
+        av.act[cp] += av.inc;  // bumped once per test, by the first of its reported pairs
+      if (db.ext) id = __ldg(db.ext + cp);
+    }
+    out_append(S, out, ra != 0u, id, ga, ra, lane);
+  }
+}
+
+// Exclusive prefix sum of x over the warp.
+__device__ __forceinline__ uint32_t warp_excl_scan(uint32_t x, uint32_t lane) {
+  uint32_t incl = x;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, incl, d);
+    if (lane >= (uint32_t)d) incl += y;
+  }
+  return incl - x;
 }
 
 // Live plane words of clause c under per-word watermarks wm[0 .. n_wm) (non-decreasing, in
@@ -273,12 +377,14 @@ __device__ __forceinline__ void live_words(const uint64_t* wm, uint32_t n_wm, ui
 // Stage A and stage B for the tile of clauses [c0, min(c0 + 32, c_hi)), whose head0 is in
 // S.ring[s]; records are staged in the warp's outbox.  EXTRA: the database has clause ids
 // apart from positions and/or activities to bump (a separate build of the kernel, so that
-// databases without them pay nothing).
-template <int MODE, int AW, bool EXTRA = false>
-__device__ __forceinline__ void test_tile(const ClauseView& db, const PlaneView& pv, WarpSmem& S,
+// databases without them pay nothing).  WIDE (with AW == 1): pv's aggregate rows are the
+// level-2 rows and stage A's bits are super-groups; wv holds the level-1 rows.
+template <int MODE, int AW, bool EXTRA = false, bool WIDE = false, typename Smem>
+__device__ __forceinline__ void test_tile(const ClauseView& db, const PlaneView& pv, Smem& S,
                                           int s, uint64_t c0, uint64_t c_hi, uint32_t lane, Outbox& out,
                                           const uint64_t* wm = nullptr, uint32_t n_wm = 0,
-                                          const ActivityView& av = ActivityView{}) {
+                                          const ActivityView& av = ActivityView{}, const WideView& wv = WideView{}) {
+  static_assert(!WIDE || AW == 1, "wide sets have one level-2 word per row");
   const uint32_t PAD = db.pad;
   const uint64_t c = c0 + lane;
   const bool act = c < c_hi;
@@ -312,23 +418,19 @@ __device__ __forceinline__ void test_tile(const ClauseView& db, const PlaneView&
 #pragma unroll
   for (int i = 0; i < AW; ++i) {
     cand[i] = af[i] | ou[i];
-    out.cand += __popc(cand[i]);  // pairs the aggregate test let through
+    if constexpr (WIDE) out.cand2 += __popc(cand[i]);  // (clause, super-group) pairs left by the level-2 test
+    else out.cand += __popc(cand[i]);                  // pairs the aggregate test let through
   }
 
-  // ---------------- stage B: exact test of the warp's candidate (clause, group) pairs
+  // ---------------- stage B: exact test of the warp's candidate (clause, group) pairs (wide
+  // sets: (clause, super-group) pairs, each first narrowed to its groups by the level-1 test)
   for (;;) {
     uint32_t cnt = 0;
 #pragma unroll
     for (int i = 0; i < AW; ++i) cnt += __popc(cand[i]);
     const uint32_t total = __reduce_add_sync(FULL, cnt);
     if (total == 0u) break;
-    uint32_t incl = cnt;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t y = __shfl_up_sync(FULL, incl, d);
-      if (lane >= (uint32_t)d) incl += y;
-    }
-    uint32_t pos = incl - cnt;
+    uint32_t pos = warp_excl_scan(cnt, lane);
 #pragma unroll
     for (int i = 0; i < AW; ++i) {
       while (cand[i] != 0u && pos < PAIR_CAP) {
@@ -339,37 +441,48 @@ __device__ __forceinline__ void test_tile(const ClauseView& db, const PlaneView&
     }
     __syncwarp();
     const uint32_t np = total < PAIR_CAP ? total : PAIR_CAP;
-    for (uint32_t p0 = 0; p0 < np; p0 += 32u) {
-      const uint32_t pa = p0 + lane;
-      const bool ha = pa < np;
-      const uint32_t ea = ha ? S.pairs[pa] : 0u;
-      const uint32_t oa = ea & 31u, ga = ea >> 5;
-      uint32_t la[8];
-      pair_head(&S.ring[s][oa * 8u], ha, PAD, la);
-      const uint32_t va = valid_bits(pv.N, ga);
-      uint32_t afa = ha ? ((MODE == GSS_MODE_ALLF) ? FULL : va) : 0u, oua = 0u;
-      word_batch8<MODE>(pv, la, ga, va, afa, oua);
-      exact_tail<MODE>(db, pv, c0 + oa, ga, va, la[7], afa, oua);
-      const uint32_t ra = afa | oua;
-      const uint64_t cp = c0 + oa;  // position of the pair's clause
-      uint32_t id = (uint32_t)cp;
-      if constexpr (EXTRA) {
-        if (ra != 0u && av.act && atomicExch(av.stamp + cp, av.epoch) != av.epoch)
-          av.act[cp] += av.inc;  // bumped once per test, by the first of its reported pairs
-        if (db.ext) id = __ldg(db.ext + cp);
+    if constexpr (WIDE) {
+      for (uint32_t p0 = 0; p0 < np; p0 += 32u) {
+        const uint32_t pa = p0 + lane;
+        const bool ha = pa < np;
+        const uint32_t ea = ha ? S.pairs[pa] : 0u;
+        const uint32_t oa = ea & 31u, sg = ea >> 5;
+        uint32_t gm = 0u;  // groups of super-group sg left by the level-1 test
+        if (ha) {
+          uint32_t la[8];
+          pair_head(&S.ring[s][oa * 8u], true, PAD, la);
+          gm = group1_mask<MODE>(db, pv, wv, la, c0 + oa, sg);
+        }
+        out.cand += __popc(gm);
+        for (;;) {  // compact the (clause, group) pairs over the warp, PAIR_CAP per round
+          const uint32_t n1 = __popc(gm);
+          const uint32_t t1 = __reduce_add_sync(FULL, n1);
+          if (t1 == 0u) break;
+          uint32_t q = warp_excl_scan(n1, lane);
+          while (gm != 0u && q < PAIR_CAP) {
+            const uint32_t b = (uint32_t)(__ffs(gm) - 1);
+            gm &= gm - 1u;
+            S.pairs2[q++] = oa | ((32u * sg + b) << 5);
+          }
+          __syncwarp();
+          exact_pairs<MODE, EXTRA>(db, pv, S, S.ring[s], S.pairs2, t1 < PAIR_CAP ? t1 : PAIR_CAP, c0, lane, out, av);
+          __syncwarp();
+        }
       }
-      out_append(S, out, ra != 0u, id, ga, ra, lane);
+    } else {
+      exact_pairs<MODE, EXTRA>(db, pv, S, S.ring[s], S.pairs, np, c0, lane, out, av);
     }
     __syncwarp();
   }
 }
 
-template <int MODE, int AW, bool EXTRA>
+template <int MODE, int AW, bool EXTRA, bool WIDE = false>
 __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c_lo, uint64_t c_hi, PlaneView pv,
                                                        gss_report* __restrict__ rec, uint64_t cap, DevStatus* st,
                                                        const uint64_t* __restrict__ wm, uint32_t n_wm,
-                                                       ActivityView av) {
-  __shared__ WarpSmem smem[TEST_WARPS];
+                                                       ActivityView av, WideView wv) {
+  using Smem = std::conditional_t<WIDE, WarpSmemWide, WarpSmem>;
+  __shared__ Smem smem[TEST_WARPS];
   __shared__ uint64_t s_wm[32 * AW];  // per-word clause watermarks (serving launches)
   if (st->bad_code) return;  // the assignment set held an invalid value code: no records
   if (n_wm > 32u * AW) n_wm = 32u * AW;
@@ -377,7 +490,7 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c
   __syncthreads();
   const uint64_t* wms = wm ? s_wm : nullptr;
   const uint32_t lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
-  WarpSmem& S = smem[wib];
+  Smem& S = smem[wib];
   const uint64_t warp_id = (uint64_t)blockIdx.x * TEST_WARPS + wib;
   const uint64_t n_warps = (uint64_t)gridDim.x * TEST_WARPS;
   const uint64_t n_tiles = (c_hi - c_lo + 31) / 32;
@@ -399,7 +512,7 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c
   };
   if (lane == 0) issue(warp_id, 0);
 
-  Outbox out{rec, cap, &st->n_records, &st->n_candidates, 0u, 0u};
+  Outbox out{rec, cap, &st->n_records, &st->n_candidates, 0u, 0u, WIDE ? &st->n_super : nullptr, 0u};
   uint32_t it = 0;
   for (uint64_t t = warp_id; t < n_tiles; t += n_warps, ++it) {
     const int s = it & 1;
@@ -415,7 +528,7 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c
       out_close(S, out, lane);
       return;
     }
-    test_tile<MODE, AW, EXTRA>(db, pv, S, s, c_lo + t * 32u, c_hi, lane, out, wms, n_wm, av);
+    test_tile<MODE, AW, EXTRA, WIDE>(db, pv, S, s, c_lo + t * 32u, c_hi, lane, out, wms, n_wm, av, wv);
     __syncwarp();
   }
   out_close(S, out, lane);
@@ -519,21 +632,44 @@ __global__ void k_batch_reset(const BatchInst* __restrict__ inst, uint32_t n_ins
   if (i < n_inst) *inst[i].st = DevStatus{};
 }
 
-template <int MODE, int AW>
+template <int MODE, int AW, bool WIDE = false>
 void launch_one(const ClauseView& db, uint64_t c_lo, uint64_t c_hi, const PlaneView& pv, gss_report* rec,
                 uint64_t cap, DevStatus* st, int grid, cudaStream_t s, const uint64_t* wm, uint32_t n_wm,
-                const ActivityView& av) {
-  if (db.ext || av.act) k_test<MODE, AW, true><<<grid, TEST_THREADS, 0, s>>>(db, c_lo, c_hi, pv, rec, cap, st, wm, n_wm, av);
-  else k_test<MODE, AW, false><<<grid, TEST_THREADS, 0, s>>>(db, c_lo, c_hi, pv, rec, cap, st, wm, n_wm, av);
+                const ActivityView& av, const WideView& wv) {
+  if (db.ext || av.act)
+    k_test<MODE, AW, true, WIDE><<<grid, TEST_THREADS, 0, s>>>(db, c_lo, c_hi, pv, rec, cap, st, wm, n_wm, av, wv);
+  else
+    k_test<MODE, AW, false, WIDE><<<grid, TEST_THREADS, 0, s>>>(db, c_lo, c_hi, pv, rec, cap, st, wm, n_wm, av, wv);
 }
 
-template <int MODE, int AW>
+template <int MODE, int AW, bool WIDE = false>
 int grid_for(int n_sms) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_test<MODE, AW, false>, TEST_THREADS, 0) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_test<MODE, AW, false, WIDE>, TEST_THREADS, 0) !=
+          cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
   return per_sm * n_sms;
+}
+
+// agg2F / agg2U: one thread per level-2 row; bit s set iff level-1 word s of the row is non-zero.
+__global__ void k_agg2(const uint32_t* __restrict__ aggF1, const uint32_t* __restrict__ aggU1, uint32_t V,
+                       uint32_t AWp1, uint32_t* __restrict__ agg2F, uint32_t* __restrict__ agg2U) {
+  const uint64_t nF = 2ull * V + 2ull, n = nF + V + 1ull;
+  for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (uint64_t)gridDim.x * blockDim.x) {
+    const bool f = r < nF;
+    const uint32_t* src = f ? aggF1 + r * AWp1 : aggU1 + (r - nF) * AWp1;
+    uint32_t b = 0u;
+    for (uint32_t i = 0; i < AWp1; i += 4) {  // AWp1 is 8, 16 or 32: 16-byte rows
+      const uint4 x = __ldg(reinterpret_cast<const uint4*>(src + i));
+      b |= (x.x != 0u ? 1u : 0u) << i;
+      b |= (x.y != 0u ? 1u : 0u) << (i + 1);
+      b |= (x.z != 0u ? 1u : 0u) << (i + 2);
+      b |= (x.w != 0u ? 1u : 0u) << (i + 3);
+    }
+    if (f) agg2F[r] = b;
+    else agg2U[r - nF] = b;
+  }
 }
 
 template <int MODE, int AW>
@@ -583,27 +719,43 @@ int test_batch_grid_size(int mode, uint32_t AWp, int n_sms) {
   return batch_grid_for<GSS_MODE_TRIGGER, 4>(n_sms);
 }
 
+cudaError_t launch_agg2(const uint32_t* aggF1, const uint32_t* aggU1, uint32_t V, uint32_t AWp1, uint32_t* agg2F,
+                        uint32_t* agg2U, cudaStream_t s) {
+  if (AWp1 < 8 || AWp1 > 32 || (AWp1 & (AWp1 - 1)) != 0) return cudaErrorInvalidValue;
+  const uint64_t n = 3ull * V + 3ull;
+  const uint64_t blocks = (n + 255) / 256;
+  k_agg2<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(aggF1, aggU1, V, AWp1, agg2F, agg2U);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_test(int mode, const ClauseView& db, uint64_t c_lo, uint64_t c_hi, const PlaneView& pv,
                         gss_report* rec, uint64_t cap, DevStatus* st, int grid, cudaStream_t s, const uint64_t* wm,
-                        uint32_t n_wm, const ActivityView& av) {
+                        uint32_t n_wm, const ActivityView& av, const WideView& wv) {
   if (c_hi <= c_lo) return cudaSuccess;
   const uint64_t tiles = (c_hi - c_lo + 31) / 32;
   const uint64_t max_blocks = (tiles + TEST_WARPS - 1) / TEST_WARPS;
   if ((uint64_t)grid > max_blocks) grid = (int)max_blocks;
   if (grid < 1) grid = 1;
+  if (wv.aggF1) {  // wide set: pv holds the level-2 rows (one word each)
+    if (pv.AWp != 1 || wm) return cudaErrorInvalidValue;
+    if (mode == GSS_MODE_ALLF) launch_one<GSS_MODE_ALLF, 1, true>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, nullptr, 0, av, wv);
+    else launch_one<GSS_MODE_TRIGGER, 1, true>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, nullptr, 0, av, wv);
+    return cudaGetLastError();
+  }
   if (mode == GSS_MODE_ALLF) {
-    if (pv.AWp == 1) launch_one<GSS_MODE_ALLF, 1>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av);
-    else if (pv.AWp == 2) launch_one<GSS_MODE_ALLF, 2>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av);
-    else launch_one<GSS_MODE_ALLF, 4>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av);
+    if (pv.AWp == 1) launch_one<GSS_MODE_ALLF, 1>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av, wv);
+    else if (pv.AWp == 2) launch_one<GSS_MODE_ALLF, 2>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av, wv);
+    else launch_one<GSS_MODE_ALLF, 4>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av, wv);
   } else {
-    if (pv.AWp == 1) launch_one<GSS_MODE_TRIGGER, 1>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av);
-    else if (pv.AWp == 2) launch_one<GSS_MODE_TRIGGER, 2>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av);
-    else launch_one<GSS_MODE_TRIGGER, 4>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av);
+    if (pv.AWp == 1) launch_one<GSS_MODE_TRIGGER, 1>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av, wv);
+    else if (pv.AWp == 2) launch_one<GSS_MODE_TRIGGER, 2>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av, wv);
+    else launch_one<GSS_MODE_TRIGGER, 4>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av, wv);
   }
   return cudaGetLastError();
 }
 
-int test_grid_size(int mode, uint32_t AWp, int n_sms) {
+int test_grid_size(int mode, uint32_t AWp, int n_sms, bool wide) {
+  if (wide) return mode == GSS_MODE_ALLF ? grid_for<GSS_MODE_ALLF, 1, true>(n_sms) : grid_for<GSS_MODE_TRIGGER, 1, true>(n_sms);
   if (mode == GSS_MODE_ALLF) {
     if (AWp == 1) return grid_for<GSS_MODE_ALLF, 1>(n_sms);
     if (AWp == 2) return grid_for<GSS_MODE_ALLF, 2>(n_sms);

@@ -240,6 +240,25 @@ def structured(scale: float = 1.0, seed: int | None = None, n_assign: int = 1024
         p_home=0.8, zipf=1.1, assign="trail groups of 32, f~U[0.30,0.70], 2% flips"))
 
 
+def wide(scale: float = 1.0, seed: int | None = None, n_assign: int = 8192, group: int = 1024) -> Instance:
+    """Wide assignment set: the single-instance database (1M vars, 4M clauses, lognormal sizes
+    median 20, sigma 1, clamped to [2, 500], Zipf(1.1) vars) against n_assign assignments in
+    trail-prefix groups of ``group`` (one simulated solver thread's successive snapshots each,
+    30-70 % assigned, the last 10 % of each prefix re-decided); 10k planted pairs."""
+    s = seed_for(6) if seed is None else seed
+    V = max(64, int(round(1_000_000 * scale)))
+    m = max(1, int(round(4_000_000 * scale)))
+    K = max(1, int(round(10_000 * scale)))
+    sizes = clause_sizes(m, "lognormal", 20.0, 1.0, 500, V, s)
+    off = offsets_from_sizes(sizes)
+    lits = clause_lits(off, V, s)
+    codes = assign_trail(V, n_assign, 0.30, 0.70, s, group=group, flip_frac=0.1)
+    pl = plant(off, lits, codes, K, s)
+    return Instance(f"wide(scale={scale:g}, N={n_assign})", V, off, lits, codes, pl, params=dict(
+        config=6, seed=s, scale=scale, sizes="lognormal(20,1)[2,500]", zipf=1.1,
+        assign=f"trail groups of {group}, f~U[0.30,0.70], 10% flips"))
+
+
 def batch_specs(n_inst: int = 64, seed: int | None = None, scale: float = 1.0) -> list[dict]:
     """Batching workload: per instance m log-uniform in [10k, 2M], V log-uniform in [5k, 500k],
     N = 128 * U{1..8}; geometric sizes as in the tiny workload, trail assignments, 100 planted.

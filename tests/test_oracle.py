@@ -37,6 +37,29 @@ def test_aggregate_theorem(tiny_instance, mode):
     assert pin_aggregate_theorem(tiny_instance, mode, group=8) == []
 
 
+@pytest.mark.parametrize("mode", [oracle.MODE_ALLF, oracle.MODE_TRIGGER])
+def test_aggregate_of_aggregates(mode):
+    """Section 7's aggregate of aggregates, which the test of sets above 4096 assignments
+    filters with: the aggregate of a 1024-assignment super-group is the union of its 32
+    groups' aggregates (value sets), and by the Theorem of Section 4.2 applied to it, every
+    (clause, group) pair whose aggregate test passes lies in a super-group whose test passes.
+    Ragged last group and super-group included."""
+    V, N, m = 150, 2 * 1024 + 100, 300
+    sizes = synth.clause_sizes(m, "geom", 1 / 7, 0, 30, V, 9)
+    off = synth.offsets_from_sizes(sizes)
+    lits = synth.clause_lits(off, V, 9)
+    codes = synth.assign_trail(V, N, 0.3, 0.7, 9, group=1024, flip_frac=0.1)
+    a32, a1024 = oracle.aggregate(codes, 32), oracle.aggregate(codes, 1024)
+    assert a1024.shape == (3, V) and a32.shape == (68, V)
+    for s in range(3):
+        assert np.array_equal(a1024[s], np.bitwise_or.reduce(a32[32 * s: 32 * s + 32], axis=0))
+    p32 = oracle.aggregate_pairs(off, lits, codes, group=32, mode=mode)
+    p1024 = oracle.aggregate_pairs(off, lits, codes, group=1024, mode=mode)
+    sup = set(map(tuple, p1024.tolist()))
+    assert all((c, g // 32) in sup for c, g in p32.tolist())
+    assert 0 < len(p1024) < 3 * m and len(p32) > 0
+
+
 def test_pair_matches_pairs(tiny_instance):
     I = tiny_instance
     R = set(map(tuple, oracle.allf_pairs(I.offsets, I.lits, I.codes).tolist()))
