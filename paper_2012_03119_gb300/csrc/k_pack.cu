@@ -12,20 +12,20 @@
 //   aggF[l] bit g = (P[l][g] != 0)      -- F is in G(l)
 //   aggU[v] bit g = some assignment of group g leaves v U   -- U is in G(v)
 //
-// Structure: four persistent CTAs per SM.  A producer warp streams the value codes
-// [N][pitch] as 2-D TMA boxes of 32 assignment rows x 128 variables (4 KiB: one
-// plane word of 128 variables) into shared memory; rows past N and variables past V
-// arrive as zeros (U).  Word w of a variable tile belongs to consumer warp w % C,
-// which owns D stages of the ring and uses them in its own program order, so
-// each full / empty mbarrier is waited on at most one phase ahead (a parity wait
-// cannot be fooled by a stage two uses behind).  The C
-// consumer warps transpose boxes: a lane takes 4 codes of each of the 32 rows; the
-// F bit (bit 1 of a code byte) and the T bit (bit 0) move to bit r % 8 of their byte
-// with one shift and one fused and-or each, and byte permutes turn four 8-row
-// accumulators into per-variable words.  Words are staged in shared memory at an odd
-// stride, so the by-lane write and the coalesced by-word read-out are both
-// bank-conflict free; the read-out derives aggF / aggU with warp ballots.  The
-// producer keeps loading the next variables while consumers write out.
+// Structure: four persistent CTAs per SM walk (variable tile, pass) units, a pass being 32
+// plane words of the tile's 128 variables.  A producer warp streams the value codes
+// [N][pitch] as 2-D TMA boxes of 32 assignment rows x 128 variables (4 KiB: one plane word
+// of 128 variables) into shared memory; rows past N and variables past V arrive as zeros
+// (U).  Word w belongs to consumer warp w % C, which owns D stages of the ring and uses them
+// in its own program order, so each full / empty mbarrier is waited on at most one phase
+// ahead (a parity wait cannot be fooled by a stage two uses behind).  The C consumer warps
+// transpose boxes: a lane takes 4 codes of each of the 32 rows; the F bit (bit 1 of a code
+// byte) and the T bit (bit 0) move to bit r % 8 of their byte with one shift and one fused
+// and-or each, and byte permutes turn four 8-row accumulators into per-variable words.
+// Words are staged in shared memory under an XOR swizzle, so the by-lane write and the
+// coalesced 16-byte read-out are both bank-conflict free; each lane ORs its words' aggregate
+// bits in registers and merges them once per pass.  The producer keeps loading the next
+// unit while consumers write out.
 #include <atomic>
 
 #include <cudaTypedefs.h>
@@ -74,20 +74,13 @@ __device__ __forceinline__ uint32_t valid_bits(uint32_t N, uint32_t w) {
   return rem >= 32u ? FULL : ((1u << rem) - 1u);
 }
 
-// Sequence number, among the boxes of consumer warp q = w % C in this CTA, of word w of
-// variable tile t (the CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...).
-template <int C>
-__device__ __forceinline__ uint32_t word_seq(uint32_t q, uint32_t t, uint32_t w, uint32_t Wd, uint32_t b,
-                                             uint32_t g) {
-  const uint32_t per_tile = Wd > q ? (Wd - q + C - 1) / C : 0u;  // words of warp q per tile
-  const uint32_t i = (t - b) / g;                                                      // tiles done before t
-  return i * per_tile + w / C;
-}
-template <int C, int D>
-__device__ __forceinline__ uint32_t stage_of(uint32_t q, uint32_t t, uint32_t w, uint32_t Wd, uint32_t b,
-                                             uint32_t g) {
-  return q + C * (word_seq<C>(q, t, w, Wd, b, g) % D);
-}
+// Units of work: (variable tile t, pass p) for u = t * n_pass + p, walked grid-stride by
+// every CTA (u = blockIdx.x, blockIdx.x + gridDim.x, ...).  A pass is PW plane words of the
+// tile's 128 variables, so wide assignment sets split into many units and the last round of
+// CTAs is short; with one pass per tile a unit is a whole tile.  (Tile-major order keeps the
+// CTAs that run at the same time on fewer tiles; pass-major order measured 3-4 % slower.)
+__device__ __forceinline__ uint32_t unit_tile(uint32_t u, uint32_t n_pass) { return u / n_pass; }
+__device__ __forceinline__ uint32_t unit_pass(uint32_t u, uint32_t n_pass) { return u % n_pass; }
 
 template <int C, int D, int MINB, int PW>
 __global__ void __launch_bounds__(32 * (C + 1), MINB) k_pack(const __grid_constant__ CUtensorMap tmap, uint32_t V,
@@ -104,6 +97,8 @@ __global__ void __launch_bounds__(32 * (C + 1), MINB) k_pack(const __grid_consta
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   const uint32_t n_vt = (V + PK_VT - 1) / PK_VT;
   const uint32_t Wd = (N + 31) / 32;  // plane words that hold assignments
+  const uint32_t n_pass = (Wp + PW - 1) / PW;
+  const uint32_t n_units = n_vt * n_pass;  // V < 2^32 and Wp <= 1024: below 2^30
   if (threadIdx.x == 0) {
     for (int s = 0; s < C * D; ++s) {
       ptx::mbar_init(&S.full[s], 1);
@@ -124,19 +119,25 @@ __global__ void __launch_bounds__(32 * (C + 1), MINB) k_pack(const __grid_consta
     if (lane == 0) {
       ptx::prefetch_tensormap(&tmap);
       uint32_t uses[C * D];  // loads issued into each stage so far
+      uint32_t cnt[C];       // boxes issued to each consumer warp so far
       for (int s = 0; s < C * D; ++s) uses[s] = 0u;
+      for (int q = 0; q < C; ++q) cnt[q] = 0u;
       bool ok = true;
-      for (uint32_t t = blockIdx.x; t < n_vt && ok; t += gridDim.x) {
-        for (uint32_t w = 0; w < Wd; ++w) {
-          // word w goes to consumer q = w % 8; its m-th word of this CTA uses stage q + 8 (m % DEPTH)
+      for (uint32_t u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+        const uint32_t t = unit_tile(u, n_pass), wc = unit_pass(u, n_pass) * PW;
+        const uint32_t we = min(wc + (uint32_t)PW, Wd);
+        for (uint32_t w = wc; w < we; ++w) {
+          // word w goes to consumer q = w % C; its m-th box of this CTA uses stage q + C (m % D)
           const uint32_t q = w % C;
-          const uint32_t s = stage_of<C, D>(q, t, w, Wd, blockIdx.x, gridDim.x);
+          uint32_t s = q;
+          if constexpr (D > 1) s += C * (cnt[q] % D);
           if (uses[s] > 0u) ok = ptx::mbar_wait(&S.empty[s], (uses[s] - 1u) & 1u);  // previous use consumed
           if (!ok || S.err) { ok = false; break; }
           ptx::mbar_expect_tx(&S.full[s], PK_BOX);
           const uint32_t row0 = word_rows ? __ldg(word_rows + w) : w * PK_ROWS;  // first code row of word w
           ptx::tma_load_2d(S.ring[s], &tmap, (int32_t)(t * PK_VT), (int32_t)row0, &S.full[s]);
           ++uses[s];
+          if constexpr (D > 1) ++cnt[q];
         }
       }
       if (!ok) {
@@ -152,32 +153,36 @@ __global__ void __launch_bounds__(32 * (C + 1), MINB) k_pack(const __grid_consta
 
   // ---------------- consumers
   uint32_t bad = 0;
-  // internal row ids of the next tile's variables, loaded one tile ahead (threads < PK_VT)
-  uint32_t next_row = 0;
-  if (threadIdx.x < PK_VT && blockIdx.x < n_vt) {
-    const uint32_t v = blockIdx.x * PK_VT + threadIdx.x;
-    next_row = v < V ? (map ? __ldg(map + v) : v) : 0u;
-  }
-  for (uint32_t t = blockIdx.x; t < n_vt; t += gridDim.x) {
+  // internal row ids of the next unit's variables, loaded one unit ahead (threads < PK_VT)
+  auto row_of = [&](uint32_t u) -> uint32_t {
+    const uint32_t v = unit_tile(u, n_pass) * PK_VT + threadIdx.x;
+    return v < V ? (map ? __ldg(map + v) : v) : 0u;
+  };
+  uint32_t next_row = (threadIdx.x < PK_VT && blockIdx.x < n_units) ? row_of(blockIdx.x) : 0u;
+  uint32_t m = 0;  // boxes this consumer warp has taken so far (its m-th sits in stage warp + C (m % D))
+  uint32_t cur_t = 0xFFFFFFFFu;
+  for (uint32_t u = blockIdx.x; u < n_units; u += gridDim.x) {
+    const uint32_t t = unit_tile(u, n_pass);
     const uint32_t v0 = t * PK_VT;
     const uint32_t nv = min((uint32_t)PK_VT, V - v0);
-    for (uint32_t wc = 0; wc < Wp; wc += PW) {
+    {
+      const uint32_t wc = unit_pass(u, n_pass) * PW;
       const uint32_t nw = min((uint32_t)PW, Wp - wc);  // 4 .. PW words in this pass
       const uint32_t lg_nw = 31u - __clz(nw);
-      if (wc == 0 && threadIdx.x < PK_VT) {  // read by the write-out after the next barrier
-        S.rowid[threadIdx.x] = next_row;
-        const uint32_t v = (t + gridDim.x) * PK_VT + threadIdx.x;
-        if (t + gridDim.x < n_vt) next_row = v < V ? (map ? __ldg(map + v) : v) : 0u;
+      if (threadIdx.x < PK_VT) {  // row ids of this unit's tile, read by the write-out after the next barrier
+        if (t != cur_t) S.rowid[threadIdx.x] = next_row;
+        if (u + gridDim.x < n_units) next_row = row_of(u + gridDim.x);
       }
+      cur_t = t;
       // aggregate bits of this lane's 4 variables over the pass's words it transposes
       uint32_t aF[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u}, aU[4] = {0u, 0u, 0u, 0u};
       for (uint32_t wl = warp; wl < nw; wl += C) {
         const uint32_t w = wc + wl;
         uint32_t f[4] = {0u, 0u, 0u, 0u}, tt[4] = {0u, 0u, 0u, 0u};
         if (w < Wd) {
-          const uint32_t m = word_seq<C>(warp, t, w, Wd, blockIdx.x, gridDim.x);
           const uint32_t s = warp + C * (m % D);
           bool ok = !S.err && ptx::mbar_wait(&S.full[s], (m / D) & 1u);
+          ++m;
           if (!__all_sync(FULL, ok)) {
             if (lane == 0 && !S.err) {
               S.err = 1;
@@ -302,9 +307,9 @@ cudaError_t launch_pack_cfg(const CUtensorMap& tmap, uint32_t V, uint32_t N, uin
     if (dev >= 0 && dev < 64) smem_set[dev].store(true, std::memory_order_release);
   }
   cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev);
-  const uint32_t n_vt = (V + PK_VT - 1) / PK_VT;
+  const uint32_t n_units = ((V + PK_VT - 1) / PK_VT) * ((Wp + PW - 1) / PW);
   const uint32_t slots = (uint32_t)MINB * (uint32_t)n_sms;
-  const uint32_t grid = n_vt < slots ? n_vt : slots;
+  const uint32_t grid = n_units < slots ? n_units : slots;
   k_pack<C, D, MINB, PW><<<grid, 32 * (C + 1), smem, s>>>(tmap, V, N, Wp, AWp, map, word_rows, P, aggF, aggU, st);
   return cudaGetLastError();
 }
