@@ -14,6 +14,10 @@ host->device inside the timed region and the records come back device->host.
 --impl reference runs the oracle (plain C on the host cores) on a bounded sample of
 the same workload, the reference arm of this comparison.
 
+Other workloads: --config structured | tiny | batch | serve, and --config wide: the same
+database against 8192 assignments (--n-assign, up to 32768) in trail groups of 1024,
+tested with two aggregate levels and compared with the same set in 4096-assignment chunks.
+
 Under torchrun each rank holds its own 4M-clause database (seed + rank) and tests the
 same assignment set: per-GPU work is fixed (weak scaling); ranks never exchange data
 except the timing barrier and the max-over-ranks reduction.
