@@ -144,6 +144,7 @@ __device__ __forceinline__ void group_batch8(const PlaneView& pv, const uint32_t
 template <int MODE>
 __device__ __forceinline__ void word_batch8(const PlaneView& pv, const uint32_t (&l)[8], uint32_t g, uint32_t valid,
                                             uint32_t& af, uint32_t& ou) {
+  g = GSS_ROW(g, pv.Wp, 0u);  // plane word (checked in the bounds build)
   uint32_t F[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) F[j] = __ldg(pv.P + (uint64_t)GSS_ROW(l[j], 2u * pv.V + 2u, 2u * pv.V) * pv.Wp + g);
@@ -200,6 +201,7 @@ __device__ __forceinline__ void exact_tail(const ClauseView& db, const PlaneView
 template <int MODE>
 __device__ __forceinline__ void group1_batch8(const WideView& wv, uint32_t V, const uint32_t (&l)[8], uint32_t sg,
                                               uint32_t& af, uint32_t& ou) {
+  sg = GSS_ROW(sg, wv.AWp1, 0u);  // word of the level-1 rows (checked in the bounds build)
   uint32_t cf[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) cf[j] = __ldg(wv.aggF1 + (uint64_t)GSS_ROW(l[j], 2u * V + 2u, 2u * V) * wv.AWp1 + sg);

@@ -1,5 +1,5 @@
 """The bounds-checked build (GSS_DEBUG_BOUNDS=1): the same results as the oracle on every path
-(plain test in both modes, batch, serving, no-allocation entry point, activity and deletion),
+(plain test in both modes, wide sets in both modes, batch, serving, activity and deletion),
 with no out-of-range gather counted.  Runs in a subprocess that builds and loads the checked
 library, so the rest of the suite keeps the release build."""
 import json
@@ -53,6 +53,15 @@ with gss.Context(inst.n_vars, report_capacity=1 << 20, max_assignments=64) as ct
 full = oracle.pairs(inst.offsets, inst.lits, inst.codes)
 keep = np.isin(full[:, 0], ids)
 ok["reduce"] = bool(np.array_equal(got, full[keep]))
+wsizes = synth.clause_sizes(600, "geom", 1 / 7, 0, 30, 400, 5)
+woff = synth.offsets_from_sizes(wsizes)
+wlits = synth.clause_lits(woff, 400, 5)
+wcodes = synth.assign_trail(400, 5000, 0.3, 0.7, 5, group=1024, flip_frac=0.1)
+for mode in (gss.GSS_MODE_ALLF, gss.GSS_MODE_TRIGGER):  # more than 4096 assignments: the level-2 path
+    with gss.Context(400, mode=mode, report_capacity=1 << 20, max_assignments=5000) as ctx:
+        ctx.add_clauses(woff, wlits)
+        got = gss.expand_reports(ctx.run(wcodes))
+    ok["wide%d" % mode] = bool(np.array_equal(got, oracle.pairs(woff, wlits, wcodes, mode)))
 enabled, errors = gss.gss_debug_bounds()
 print(json.dumps({"ok": ok, "enabled": enabled, "errors": errors}))
 """
