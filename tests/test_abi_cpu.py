@@ -84,3 +84,30 @@ def test_expand_reports_host_helper():
     rec[0] = (5, 1, 0b101)
     rec[1] = (2, 0, 1 << 31)
     assert gss.expand_reports(rec).tolist() == [[2, 31], [5, 32], [5, 34]]
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every public struct of include/gss.h has the size and field offsets that the ctypes
+    binding declares (compiled with the host C compiler; no device needed)."""
+    structs = [gss.gss_config, gss.gss_stats, gss.gss_batch_info, gss.gss_server_config, gss.gss_request_info,
+               gss.gss_server_stats]
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "gss.h"', "int main(void) {"]
+    for st in structs:
+        n = st.__name__
+        lines.append(f'  printf("{n} size %zu\\n", sizeof({n}));')
+        for f, _ in st._fields_:
+            lines.append(f'  printf("{n} {f} %zu\\n", offsetof({n}, {f}));')
+    lines.append('  printf("gss_report size %zu\\n", sizeof(gss_report));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for st in structs:
+        n = st.__name__
+        assert got[(n, "size")] == ctypes.sizeof(st), n
+        for f, _ in st._fields_:
+            assert got[(n, f)] == getattr(st, f).offset, (n, f)
+    assert got[("gss_report", "size")] == gss.REPORT_DTYPE.itemsize == 12
