@@ -163,7 +163,10 @@ int gss_add_clauses(gss_ctx* ctx, const uint64_t* offsets, uint64_t n_clauses, c
  *   values host, row-major [n_assign][n_vars] bytes, 0 = U, 1 = T, 2 = F.
  * 0 <= n_assign <= cfg.max_assignments.  Assignments 32g .. 32g+31 form
  * group g; grouping assignments of one solver thread together (Section 4.3)
- * makes the group prefilter effective but never changes results.
+ * makes the group prefilter effective but never changes results.  Above
+ * GSS_MAX_NARROW_ASSIGNMENTS, assignments 1024s .. 1024s+1023 also form
+ * super-group s, with one more aggregate word per literal (Section 7); the
+ * records are the same.
  * Queued on the stream (the host buffer is copied before return).  A value
  * code above 2 is detected on the device and reported as GSS_E_INVAL by the
  * next gss_fetch_reports / gss_report_count, with no records.
