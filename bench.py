@@ -695,7 +695,7 @@ def main():
                         "test_us": t_test * 1e6},
         "ingest": {"seconds": ingest_s, "clauses": m, "lits": inst.n_lits,
                    "GB_per_s": (8 * (m + 1) + 4 * inst.n_lits) / ingest_s / 1e9},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": (3 if N > gss.GSS_MAX_NARROW_ASSIGNMENTS else 2) * args.steps,  # pack (+ level 2) + test
         "records": n_records, "pairs": int(len(pairs)), "planted_found": planted_ok,
         "aggregate_test": aggregate,
         "clocks": clk,
