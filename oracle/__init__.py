@@ -129,22 +129,22 @@ def pair(offsets, lits, codes_row, c: int, mode: int = MODE_ALLF, mutant: int = 
     return bool(_load(mutant).gss_oracle_pair(mode, _p(off), _p(lt), c, _p(row)))
 
 
-def aggregate(codes, group: int = 32) -> np.ndarray:
+def aggregate(codes, group: int = 32, mutant: int = 0) -> np.ndarray:
     """Section 4.2 aggregate assignments: uint8 [ceil(N/group), V], bits T=1, F=2, U=4."""
     cd = np.ascontiguousarray(codes, dtype=np.uint8)
     N, V = cd.shape
     G = (N + group - 1) // group
     out = np.empty((G, V), dtype=np.uint8)
-    _load().gss_oracle_aggregate(V, N, _p(cd), group, _p(out))
+    _load(mutant).gss_oracle_aggregate(V, N, _p(cd), group, _p(out))
     return out
 
 
-def aggregate_pairs(offsets, lits, codes, group: int = 32, mode: int = MODE_ALLF) -> np.ndarray:
+def aggregate_pairs(offsets, lits, codes, group: int = 32, mode: int = MODE_ALLF, mutant: int = 0) -> np.ndarray:
     """(clause, group) pairs on which the aggregate test of Section 4.2 is positive, sorted."""
     off = _arr(offsets, np.uint64)
     lt = _arr(lits, np.uint32)
-    agg = aggregate(codes, group)
-    lib = _load()
+    agg = aggregate(codes, group, mutant=mutant)
+    lib = _load(mutant)
     out = []
     for g in range(agg.shape[0]):
         row = np.ascontiguousarray(agg[g])

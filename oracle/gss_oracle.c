@@ -27,8 +27,9 @@
  *
  * Parity pinning: every entry point is pinned by the CPU tests (worked
  * examples of Sections 3.3 and 4.2, brute force over all 3^V assignments with
- * closed-form counts, invariants, a recount in another loop order, and the
- * Theorem of Section 4.2 as a property).  ORACLE_MUTANT builds deliberately
+ * closed-form counts, the aggregate tests of both modes against their set
+ * definitions over every small group of assignments, invariants, a recount in
+ * another loop order, and the Theorem of Section 4.2 as a property).  ORACLE_MUTANT builds deliberately
  * wrong variants that those pins must reject.
  */
 #include <stdint.h>
@@ -59,7 +60,7 @@ static uint8_t literal_value(const uint8_t* A, uint32_t l) {
   return negated ? negate(A[v]) : A[v];
 }
 
-/* Section 3.3: "if all literals of this clause are False, then this clause would have been in conflict". */
+/* Section 3.3: a clause every literal of which is F under A would have been the conflicting clause. */
 static int clause_all_false(const uint32_t* lits, uint64_t b, uint64_t e, const uint8_t* A) {
 #if ORACLE_MUTANT == 2 /* drops the last literal */
   if (e > b) --e;
@@ -211,7 +212,11 @@ int gss_oracle_aggregate_test(int mode, const uint64_t* off, const uint32_t* lit
   for (uint64_t k = b; k < e; ++k) {
     uint8_t g = aggregate_literal(Gv, lits[k]);
     if (mode == MODE_ALLF) {
+#if ORACLE_MUTANT == 7 /* F or U in G(l) taken for F in G(l) */
+      if (!(g & 6)) return 0;
+#else
       if (!(g & 2)) return 0;
+#endif
     } else {
       if (!(g & 6)) return 0;
       if (g & 2) ++n_f;

@@ -6,8 +6,8 @@
 // answer directly, one row per LITERAL:
 //   P[2v][w]   bit j = (A_{32w+j}(v) == F)   -- literal v is F
 //   P[2v+1][w] bit j = (A_{32w+j}(v) == T)   -- literal not v is F
-// U sets neither bit (the paper's "isTrue might be set or not for U" is resolved
-// to 0, and not-v is read from isTrue masked by isSet rather than ~isTrue).
+// U sets neither bit (Section 3.4 leaves isTrue free for U; here it is 0, and not-v
+// is read from isTrue masked by isSet rather than from ~isTrue).
 // Section 4.2's aggregate of a 32-assignment group g is derived in the same pass:
 //   aggF[l] bit g = (P[l][g] != 0)      -- F is in G(l)
 //   aggU[v] bit g = some assignment of group g leaves v U   -- U is in G(v)

@@ -86,12 +86,12 @@ def pin_golden(name: str, mutant: int = 0) -> list[str]:
             off, lt = _one_clause_db(ch["lits"])
             codes = np.stack(ch["group"])
             for key, want in ch["expect"].items():
-                got = len(oracle.aggregate_pairs(off, lt, codes, group=len(codes), mode=modes[key])) > 0
+                got = len(oracle.aggregate_pairs(off, lt, codes, group=len(codes), mode=modes[key], mutant=mutant)) > 0
                 if int(got) != want[0]:
                     fails.append(f"{name}: {ch['text']}: aggregate {key} got {int(got)}")
         elif ch["kind"] == "expect_aggregate":
             codes = np.stack(ch["group"])
-            agg = oracle.aggregate(codes, group=len(codes))[0]
+            agg = oracle.aggregate(codes, group=len(codes), mutant=mutant)[0]
             for v, want in ch["expect"].items():
                 got = {c for bit, c in ((1, "T"), (2, "F"), (4, "U")) if agg[v] & bit}
                 if got != want:
@@ -245,4 +245,55 @@ def pin_aggregate_theorem(inst, mode: int, group: int = 32, mutant: int = 0, max
         if (c, a // group) not in aggp:
             fails.append(f"pair ({c},{a}) passes but its group aggregate does not")
             break
+    return fails
+
+
+def _member_values(group_rows: np.ndarray, lit: int) -> set[str]:
+    """The values the members of a group give literal lit = 2v + s, read member by member
+    (Section 3.1: the literal takes v's value when s = 0 and its negation when s = 1)."""
+    v, neg = lit >> 1, lit & 1
+    name = {0: "U", 1: "T", 2: "F"}
+    flip = {"T": "F", "F": "T", "U": "U"}
+    vals = {name[int(x)] for x in group_rows[:, v]}
+    return {flip[x] for x in vals} if neg else vals
+
+
+def aggregate_by_members(group_rows: np.ndarray, clause, mode: int) -> bool:
+    """Section 4.2 on sets, without the oracle's bit encoding: G(l) is the set of values the
+    members give l.  All-F (the all-F restriction of aggregateTrigger): F is in G(l) for every
+    literal.  Trigger (the Definition of Section 4.2): F or U is in G(l) for every literal, and
+    F is in G(l) for at least s - 1 of them."""
+    sets = [_member_values(group_rows, l) for l in clause]
+    if mode == oracle.MODE_ALLF:
+        return all("F" in g for g in sets)
+    return all(("F" in g) or ("U" in g) for g in sets) and sum("F" in g for g in sets) + 1 >= len(clause)
+
+
+def pin_aggregate_brute_force(n_vars: int, sizes=(2, 3), mutant: int = 0, max_groups: int | None = None) -> list[str]:
+    """Both directions of the aggregate tests: for every group of distinct assignments (of each
+    size in `sizes`) out of the 3^V, and every clause of 1..3 distinct literals, the oracle's
+    aggregate test is positive exactly when the set definition above says so."""
+    fails = []
+    A = all_assignments(n_vars)
+    clauses = all_small_clauses(n_vars, 3)
+    off = np.zeros(len(clauses) + 1, np.uint64)
+    off[1:] = np.cumsum([len(c) for c in clauses])
+    lits = np.array([l for c in clauses for l in c], np.uint32)
+    for k in sizes:
+        groups = list(itertools.combinations(range(len(A)), k))
+        if max_groups is not None and len(groups) > max_groups:
+            pick = np.random.default_rng(k).choice(len(groups), size=max_groups, replace=False)
+            groups = [groups[i] for i in sorted(pick)]
+        codes = np.concatenate([A[list(g)] for g in groups])  # group j = rows k*j .. k*j + k - 1
+        for mode in (oracle.MODE_ALLF, oracle.MODE_TRIGGER):
+            got = set(map(tuple, oracle.aggregate_pairs(off, lits, codes, group=k, mode=mode, mutant=mutant).tolist()))
+            for j, g in enumerate(groups):
+                rows = A[list(g)]
+                for ci, cl in enumerate(clauses):
+                    want = aggregate_by_members(rows, cl, mode)
+                    if ((ci, j) in got) != want:
+                        fails.append(f"V={n_vars} group {g} clause {cl} mode {mode}: aggregate test "
+                                     f"{'positive' if not want else 'negative'}, set definition says {want}")
+                        if len(fails) > 5:
+                            return fails
     return fails

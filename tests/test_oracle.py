@@ -4,7 +4,8 @@ import pytest
 
 import oracle
 import synth
-from pins import (pin_aggregate_theorem, pin_brute_force, pin_golden, pin_invariants, pin_monotone)
+from pins import (pin_aggregate_brute_force, pin_aggregate_theorem, pin_brute_force, pin_golden, pin_invariants,
+                  pin_monotone)
 
 GOLDEN = ["sec33_trigger_example.txt", "sec36_two_thread_example.txt", "sec42_aggregate_examples.txt"]
 
@@ -77,7 +78,8 @@ def test_empty_inputs():
 
 # Deliberately wrong oracle builds: each must be rejected by at least one pin.
 MUTANTS = {1: "wrong sign convention", 2: "drops last literal", 3: "treats U as F",
-           4: "skips first literal", 5: "exists instead of for-all", 6: "trigger threshold off by one"}
+           4: "skips first literal", 5: "exists instead of for-all", 6: "trigger threshold off by one",
+           7: "aggregate all-F takes F or U in G(l)"}
 
 
 @pytest.mark.parametrize("mutant", sorted(MUTANTS))
@@ -86,9 +88,19 @@ def test_pins_reject_mutant(mutant, tiny_instance):
     for name in GOLDEN:
         fails += pin_golden(name, mutant=mutant)
     fails += pin_brute_force(3, mutant=mutant)
+    fails += pin_aggregate_brute_force(2, mutant=mutant)
     if mutant != 6:
         fails += pin_invariants(tiny_instance, mutant=mutant)
     assert fails, f"mutant {mutant} ({MUTANTS[mutant]}) passed every pin"
+
+
+def test_aggregate_allf_mutant_is_caught_by_the_set_pin_alone():
+    """Mutant 7 changes only the all-F aggregate test, which the Theorem of Section 4.2 cannot
+    see (it only rules out false negatives): the two-sided pin rejects it by itself, while the
+    Theorem still holds for it."""
+    inst = synth.tiny()
+    assert pin_aggregate_theorem(inst, oracle.MODE_ALLF, group=8, mutant=7, max_clauses=500) == []
+    assert pin_aggregate_brute_force(2, mutant=7) != []
 
 
 # ---------------------------------------------------------------- clause activity (Section 3.6)
@@ -184,3 +196,11 @@ def test_reduce_removes_exactly_the_pairs_of_deleted_clauses():
     # clauses added after a reduction take new ids; ids are never reused
     first = a.add(inst.offsets[:11], inst.lits[: int(inst.offsets[10])])
     assert first == inst.n_clauses and a.ids[-1] == inst.n_clauses + 9
+
+
+@pytest.mark.parametrize("n_vars", [1, 2, 3])
+def test_aggregate_tests_match_set_definitions(n_vars):
+    """Section 4.2, both directions and both modes: over every group of two and three distinct
+    assignments out of the 3^V, every clause of up to three literals passes the oracle's
+    aggregate test exactly when the definitions, evaluated on the members' value sets, say so."""
+    assert pin_aggregate_brute_force(n_vars) == []
