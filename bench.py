@@ -324,10 +324,10 @@ def run_batch(args):
                         "launches_per_step": 2 * len(insts)},
            "speedup_vs_separate": t_sep / t_batch, "identical_records": same, "autotune": info,
            "first_run_s": setup_s, "gpu_launches": (len(insts) + 2) * args.steps}
-    print(json.dumps(out), flush=True)
     b.close()
     for c in ctxs:
         c.close()
+    return out
 
 
 SERVE_WORKLOAD = ("serving: 1M vars, resident DB grows 2M -> 6M clauses (80 batches of 50k, one per 50 ms), "
@@ -503,7 +503,26 @@ def run_serve(args):
            "speedup_vs_one_launch_per_request": (n_sat / t_sat) / (n_one / t_one),
            "identical_records": same, "clocks": clk,
            "gpu_launches": 3 * (s3["launches"] - s0["launches"])}
-    print(json.dumps(out), flush=True)
+    return out
+
+
+def batch_summary(b: dict) -> dict:
+    """The batching line's figures that the default line carries."""
+    return {"workload": b["config"]["workload"], "value": b["value"], "unit": b["unit"],
+            "ms_per_step": b["ms_per_step"], "pair_tests_per_step": b["config"]["pair_tests_per_step"],
+            "separate": b["separate"], "speedup_vs_separate": b["speedup_vs_separate"],
+            "identical_records": b["identical_records"], "autotune": b["autotune"], "steps": b["steps"]}
+
+
+def serve_summary(v: dict) -> dict:
+    """The serving line's figures that the default line carries."""
+    ol = v["open_loop"]
+    return {"workload": v["config"]["workload"], "value": v["value"], "unit": v["unit"],
+            "latency_us": ol["latency_us"], "requests": ol["requests"], "dropped": ol["dropped"],
+            "mean_batch_words": ol["mean_batch_words"], "saturated": v["saturated"],
+            "one_launch_per_request": v["one_launch_per_request"],
+            "speedup_vs_one_launch_per_request": v["speedup_vs_one_launch_per_request"],
+            "identical_records": v["identical_records"], "clocks": v["clocks"]}
 
 
 def main():
@@ -518,6 +537,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--ref-assignments", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="single workload only: skip the batching and serving runs the default line carries")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="requests/s over all simulated solver threads")
     ap.add_argument("--serve-threads", type=int, default=32)
     ap.add_argument("--serve-sat-requests", type=int, default=1024)
@@ -534,11 +555,11 @@ def main():
 
     if args.config == "batch" and args.impl != "reference":
         if rank == 0:
-            run_batch(args)
+            print(json.dumps(run_batch(args)), flush=True)
         return
     if args.config == "serve" and args.impl != "reference":
         if rank == 0:
-            run_serve(args)
+            print(json.dumps(run_serve(args)), flush=True)
         return
 
     if args.impl == "reference":
@@ -676,6 +697,11 @@ def main():
                  "kernel": "k_test",
                  "peak_source": f"{pk['source']} hbm_gbs"},
     }
+    for k, t in (("pack", t_pack), ("test", t_test)):
+        # the fraction on the bytes DRAM really moved (ncu), beside the one on algorithmic bytes:
+        # an early-exit test reads far fewer literals than the algorithmic count assumes
+        tr = roof[k]["traffic"]
+        roof[k]["frac_traffic"] = tr / t / 1e9 / pk["hbm_gbs"] if tr else None
     dominant = "pack" if t_pack >= t_test else "test"
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": warmup,
@@ -703,8 +729,17 @@ def main():
     if split:
         out["narrow_split"] = split
     ctx.close()
+    del d_codes, h_codes
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(inst)
+    if world == 1 and args.config == "single" and args.scale == 1.0 and args.mode == "allf" and not args.no_extras:
+        # the batching and serving workloads, on the same GPU, so that one run records every form
+        del inst
+        torch.cuda.empty_cache()
+        bargs = argparse.Namespace(**{**vars(args), "steps": min(args.steps, 20), "warmup": 3})
+        out["batch"] = batch_summary(run_batch(bargs))
+        torch.cuda.empty_cache()
+        out["serve"] = serve_summary(run_serve(bargs))
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:

@@ -370,7 +370,9 @@ int gss_export_clauses(gss_ctx* ctx, uint64_t* offsets, uint64_t cap_clauses, ui
  * Every call on a device reuses the same array and leaves its contents behind, so calls
  * that may overlap on the GPU (other streams, other host threads) must not be issued:
  * they would race on it.  The first call on a device looks up the array's device address
- * (with that device current); make that first call before any stream capture.
+ * (with that device current); make that first call before any stream capture.  A call in
+ * a new context of the device (after cudaDeviceReset) looks the address up again, so make
+ * the first call after a reset before any stream capture as well.
  */
 int gss_test_noalloc(const uint64_t* d_offsets, uint64_t n_clauses, const uint32_t* d_lits, uint32_t n_vars,
                      const uint8_t* d_values, uint64_t pitch, uint32_t n_assign, uint32_t mode, gss_report* d_out,

@@ -46,6 +46,9 @@ struct PlaneView {
   const uint32_t* aggU;
   uint32_t Wp, AWp, N;
   uint32_t V;  // rows: P and aggF 2V + 2, aggU V + 1
+  // Serving: bits of plane word w that hold real assignments (wvalid[w], w < ceil(N / 32));
+  // the other rows of a word are U padding and must not report.  nullptr: every row below N.
+  const uint32_t* wvalid = nullptr;
 };
 
 // Wide assignment sets (more than 4096 assignments; Section 7's aggregate of aggregates): the
@@ -93,10 +96,13 @@ cudaError_t launch_pack(const uint8_t* codes, uint64_t pitch, uint32_t V, uint32
                         cudaStream_t s);
 
 // As launch_pack, but plane word w takes its 32 assignments from code rows
-// word_rows[w] .. word_rows[w] + 31 (device array) of a code array of code_rows rows.
+// word_rows[w] .. word_rows[w] + 31 (device array) of a code array of code_rows rows, of
+// which only the rows of bits word_valid[w] are real assignments (word_valid nullable: all
+// rows below N): the U padding of a word then leaves no trace in aggU.
 cudaError_t launch_pack_rows(const uint8_t* codes, uint64_t pitch, uint32_t V, uint32_t N, uint32_t Wp,
                              uint32_t AWp, const uint32_t* map, const uint32_t* word_rows, uint32_t code_rows,
-                             uint32_t* P, uint32_t* aggF, uint32_t* aggU, DevStatus* st, cudaStream_t s);
+                             uint32_t* P, uint32_t* aggF, uint32_t* aggU, DevStatus* st, cudaStream_t s,
+                             const uint32_t* word_valid = nullptr);
 
 // Ingest, in order: validate a batch (offsets -> db offsets at off_db[n0 + 1 ..], literal range);
 // on the first batch rank the variables hot-first (map[v] = internal id; scratch holds

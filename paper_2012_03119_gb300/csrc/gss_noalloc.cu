@@ -12,7 +12,10 @@
 // until the process exits, and every call on a device reuses it, so calls that overlap on
 // the GPU (two streams, two threads) race on it.  Host code cannot use the array's name as
 // a device address; the first call on each device asks the runtime for the address
-// (cudaGetSymbolAddress, with that device current) and keeps it.
+// (cudaGetSymbolAddress, with that device current) and keeps it together with the identity
+// of the device's current context.  A later call in another context of that device (after
+// a cudaDeviceReset, say) looks the address up again instead of using the old one.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -30,6 +33,32 @@ namespace {
 constexpr int MAX_DEVICES = 64;
 std::mutex g_setup_mutex;
 unsigned char* g_scratch_addr[MAX_DEVICES] = {};
+unsigned long long g_scratch_ctx[MAX_DEVICES] = {};  // id of the context the address belongs to
+
+// Identity of the calling thread's current context (driver entry points fetched through the
+// runtime, so the library links no driver library); 0 when there is none or it cannot be told.
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {  // under g_setup_mutex
+    looked_up = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(p);
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(p);
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 int say(char* buf, size_t len, int code, const char* msg) {
   if (buf && len) {
@@ -41,14 +70,17 @@ int say(char* buf, size_t len, int code, const char* msg) {
 
 uint64_t up256(uint64_t x) { return (x + 255) / 256 * 256; }
 
-// Address of this device's scratch array (looked up once per device, that device current).
+// Address of this device's scratch array, looked up with that device current on the first
+// call and again whenever the device's current context is not the one it was looked up in.
 cudaError_t scratch_for(int dev, unsigned char** out) {
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
+  const unsigned long long ctx = current_context_id();
+  if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
     void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // makes the primary context current
     if (e != cudaSuccess) return e;
     g_scratch_addr[dev] = static_cast<unsigned char*>(p);
+    g_scratch_ctx[dev] = current_context_id();
   }
   *out = g_scratch_addr[dev];
   return cudaSuccess;

@@ -201,9 +201,12 @@ cudaError_t start_launch(gss_server* v, Lane& L) {
   if (e == cudaSuccess) e = cudaMemsetAsync(&L.d_out->st, 0, 2 * sizeof(DevStatus), L.s);
   if (e == cudaSuccess)
     e = launch_pack_rows(v->d_slots, v->Vp, v->V, N, Wp, AWp, v->map.load(), L.d_in->rows, v->n_slots * 32u, L.P,
-                         L.aggF, L.aggU, &L.d_out->pack_st, L.s);
+                         L.aggF, L.aggU, &L.d_out->pack_st, L.s, L.d_in->nmask);
   if (e == cudaSuccess && max_wm) {
-    const PlaneView pv{L.P, L.aggF, L.aggU, Wp, AWp, N, v->V};
+    // the U rows that pad a request of fewer than 32 assignments make no record (in trigger
+    // mode a unit clause triggers on them), so they never count against the launch's capacity
+    PlaneView pv{L.P, L.aggF, L.aggU, Wp, AWp, N, v->V};
+    pv.wvalid = L.d_in->nmask;
     e = launch_test((int)v->mode, v->db, 0, max_wm, pv, L.rec, L.cap, &L.d_out->st, v->grid, L.s, L.d_in->wm, k);
   }
   if (e == cudaSuccess) e = cudaLaunchHostFunc(L.s, lane_tested, &L);
@@ -231,7 +234,8 @@ void finish_launch(gss_server* v, Lane& L) {
     v->reports += cnt;
     q.done = true;
     q.overflow = overflow;
-    q.bad = ((pst.bad_code >> w) & 1u) != 0u || st.timeout != 0u || pst.timeout != 0u;  // spoils only itself
+    // an invalid code spoils only its own request; a timeout or an overflow spoils the whole launch
+    q.bad = ((pst.bad_code >> w) & 1u) != 0u || st.timeout != 0u || pst.timeout != 0u;
     q.t_done = now;
     v->lat_us.push_back(std::chrono::duration<double, std::micro>(q.t_done - q.t_submit).count());
     v->pair_tests += q.wm * (uint64_t)q.n;

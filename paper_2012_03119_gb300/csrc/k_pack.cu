@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(32 * (C + 1), MINB) k_pack(const __grid_consta
                                                         uint32_t N, uint32_t Wp, uint32_t AWp,
                                                         const uint32_t* __restrict__ map,
                                                         const uint32_t* __restrict__ word_rows,
+                                                        const uint32_t* __restrict__ word_valid,
                                                         uint32_t* __restrict__ P, uint32_t* __restrict__ aggF,
                                                         uint32_t* __restrict__ aggU, DevStatus* st) {
   // the consumer threads load the row ids of a whole tile: one thread per variable
@@ -223,7 +224,9 @@ __global__ void __launch_bounds__(32 * (C + 1), MINB) k_pack(const __grid_consta
         x[5] = __byte_perm(tc, td, 0x5410);
         x[6] = __byte_perm(fc, fd, 0x7632);
         x[7] = __byte_perm(tc, td, 0x7632);
-        const uint32_t bit = 1u << (w & 31u), vw = valid_bits(N, w);  // bit of the word in its aggregate word
+        // bit of the word in its aggregate word; rows of the word that are real assignments
+        const uint32_t bit = 1u << (w & 31u);
+        const uint32_t vw = valid_bits(N, w) & ((word_valid && w < Wd) ? __ldg(word_valid + w) : FULL);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const uint32_t r = 8u * lane + (uint32_t)j;  // row of (variable 4 lane + j / 2, sign j % 2)
@@ -294,8 +297,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // Launch k_pack<C, D, MINB> over every variable tile: MINB persistent CTAs per SM.
 template <int C, int D, int MINB, int PW = PK_PASS>
 cudaError_t launch_pack_cfg(const CUtensorMap& tmap, uint32_t V, uint32_t N, uint32_t Wp, uint32_t AWp,
-                            const uint32_t* map, const uint32_t* word_rows, uint32_t* P, uint32_t* aggF,
-                            uint32_t* aggU, DevStatus* st, cudaStream_t s) {
+                            const uint32_t* map, const uint32_t* word_rows, const uint32_t* word_valid, uint32_t* P,
+                            uint32_t* aggF, uint32_t* aggU, DevStatus* st, cudaStream_t s) {
   const size_t smem = sizeof(PackSmem<C, D, PW>) + 128;
   int dev = 0, n_sms = 1;
   cudaGetDevice(&dev);
@@ -310,7 +313,8 @@ cudaError_t launch_pack_cfg(const CUtensorMap& tmap, uint32_t V, uint32_t N, uin
   const uint32_t n_units = ((V + PK_VT - 1) / PK_VT) * ((Wp + PW - 1) / PW);
   const uint32_t slots = (uint32_t)MINB * (uint32_t)n_sms;
   const uint32_t grid = n_units < slots ? n_units : slots;
-  k_pack<C, D, MINB, PW><<<grid, 32 * (C + 1), smem, s>>>(tmap, V, N, Wp, AWp, map, word_rows, P, aggF, aggU, st);
+  k_pack<C, D, MINB, PW><<<grid, 32 * (C + 1), smem, s>>>(tmap, V, N, Wp, AWp, map, word_rows, word_valid, P, aggF,
+                                                          aggU, st);
   return cudaGetLastError();
 }
 
@@ -318,7 +322,8 @@ cudaError_t launch_pack_cfg(const CUtensorMap& tmap, uint32_t V, uint32_t N, uin
 
 cudaError_t launch_pack_rows(const uint8_t* codes, uint64_t pitch, uint32_t V, uint32_t N, uint32_t Wp,
                              uint32_t AWp, const uint32_t* map, const uint32_t* word_rows, uint32_t code_rows,
-                             uint32_t* P, uint32_t* aggF, uint32_t* aggU, DevStatus* st, cudaStream_t s) {
+                             uint32_t* P, uint32_t* aggF, uint32_t* aggU, DevStatus* st, cudaStream_t s,
+                             const uint32_t* word_valid) {
   if (V == 0 || N == 0) {  // no kernel: the PAD literal rows still have to be set (the kernel writes them otherwise)
     cudaError_t e = cudaMemsetAsync(P + 2ull * V * Wp, 0xFF, 2ull * Wp * sizeof(uint32_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(aggF + 2ull * V * AWp, 0xFF, 2ull * AWp * sizeof(uint32_t), s);
@@ -337,8 +342,8 @@ cudaError_t launch_pack_rows(const uint8_t* codes, uint64_t pitch, uint32_t V, u
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
-  return launch_pack_cfg<PK_CONSUMERS, PK_DEPTH, PK_MINB>(tmap, V, N, Wp, AWp, map, word_rows, P, aggF, aggU, st,
-                                                         s);
+  return launch_pack_cfg<PK_CONSUMERS, PK_DEPTH, PK_MINB>(tmap, V, N, Wp, AWp, map, word_rows, word_valid, P, aggF,
+                                                         aggU, st, s);
 }
 
 cudaError_t launch_pack(const uint8_t* codes, uint64_t pitch, uint32_t V, uint32_t N, uint32_t Wp, uint32_t AWp,

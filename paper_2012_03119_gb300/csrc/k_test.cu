@@ -327,7 +327,7 @@ __device__ __forceinline__ void exact_pairs(const ClauseView& db, const PlaneVie
     const uint32_t oa = ea & 31u, ga = ea >> 5;
     uint32_t la[8];
     pair_head(ring + oa * 8u, ha, db.pad, la);
-    const uint32_t va = valid_bits(pv.N, ga);
+    const uint32_t va = valid_bits(pv.N, ga) & ((pv.wvalid && ha) ? __ldg(pv.wvalid + ga) : FULL);  // real rows only
     uint32_t afa = ha ? ((MODE == GSS_MODE_ALLF) ? FULL : va) : 0u, oua = 0u;
     word_batch8<MODE>(pv, la, ga, va, afa, oua);
     exact_tail<MODE>(db, pv, c0 + oa, ga, va, la[7], afa, oua);

@@ -23,9 +23,9 @@ def test_single_instance_full_size():
     assert contains_all(got, inst.planted)
 
 
-def test_structured_full_size_sampled():
-    """10M vars, 10M clauses (L ~ 660M), 1024 assignments: the oracle checks a 64-assignment
-    sample in full, and every GPU pair of a further random sample one by one."""
+def test_structured_full_size():
+    """10M vars in 1,000 communities, 10M clauses (L ~ 660M), 1024 assignments: the whole set
+    against the oracle (10.2 G pair tests on the host cores)."""
     inst = synth.structured(scale=1.0)
     with gss.Context(inst.n_vars, report_capacity=1 << 26) as ctx:
         ctx.add_clauses(inst.offsets, inst.lits)
@@ -33,20 +33,13 @@ def test_structured_full_size_sampled():
     check_records(rec, inst.n_clauses, inst.n_assign)
     got = gss.expand_reports(rec)
     assert contains_all(got, inst.planted)
-    lo, hi = 480, 544  # two whole 32-assignment groups
-    want = oracle.allf_pairs(inst.offsets, inst.lits, inst.codes, a_range=(lo, hi))
-    sub = got[(got[:, 1] >= lo) & (got[:, 1] < hi)]
-    assert np.array_equal(sub, want)
-    rng = np.random.default_rng(0)
-    for i in rng.choice(len(got), size=min(2000, len(got)), replace=False):
-        c, a = got[i]
-        assert oracle.pair(inst.offsets, inst.lits, inst.codes[a], int(c))
+    want = oracle.allf_pairs(inst.offsets, inst.lits, inst.codes)
+    assert got.shape == want.shape and np.array_equal(got, want)
 
 
 def test_batch_full_size():
     """The 64-instance batching workload at full size (18.6M clauses, 12.5 G pair tests) in one
-    graph run: every instance's planted pairs are found, and 17 instances (the largest, the
-    smallest and a spread between them) equal the oracle in full."""
+    graph run: every instance equals the oracle in full."""
     insts = [synth.batch_instance(sp) for sp in synth.batch_specs(64)]
     with gss.Batch() as b:
         for I in insts:
@@ -55,21 +48,18 @@ def test_batch_full_size():
             b.set_assignments(i, I.codes)
         b.test()
         got = [gss.expand_reports(b.fetch_reports(i)) for i in range(len(insts))]
-    by_size = sorted(range(len(insts)), key=lambda i: insts[i].n_clauses * insts[i].n_assign)
-    full = set(by_size[:: max(1, len(by_size) // 14)]) | {by_size[0], by_size[-1]}
-    for i, (I, g) in enumerate(zip(insts, got)):
+    for I, g in zip(insts, got):
         assert contains_all(g, I.planted), I.name
-        assert len(g) == 0 or (g[:, 0].max() < I.n_clauses and g[:, 1].max() < I.n_assign)
-        if i in full:
-            want = oracle.allf_pairs(I.offsets, I.lits, I.codes)
-            assert g.shape == want.shape and np.array_equal(g, want), I.name
+        want = oracle.allf_pairs(I.offsets, I.lits, I.codes)
+        assert g.shape == want.shape and np.array_equal(g, want), I.name
 
 
 def test_serve_full_size():
-    """The serving workload's database (1M vars, 2M clauses growing by 50k batches) with the
-    bench's server shape; requests admitted between batches are checked against the oracle on
-    the database prefix their watermark names."""
-    w = synth.serve_workload(scale=1.0, n_batches=6)
+    """The serving workload at full size: 1M vars, the database grows from 2M to 6M clauses in
+    80 batches of 50k, with the bench's server shape.  Requests admitted along the way, and
+    three at the final 6M-clause watermark, equal the oracle on the database prefix their
+    watermark names."""
+    w = synth.serve_workload(scale=1.0)
     snaps = synth.serve_snapshots(w.n_vars, 4, seed=synth.seed_for(4, 1))
     final = len(w.offsets) - 1
     with gss.Server(w.n_vars, max_clauses=final + 1, max_lits=int(w.offsets[-1]) + 1, slots=64, lanes=3,
@@ -78,14 +68,18 @@ def test_serve_full_size():
         ids = [(srv.submit(snaps[0], wait_us=10_000_000), 0)]
         for b in range(w.n_batches):
             srv.add_clauses(*w.csr(*w.batch_range(b)))
-            ids.append((srv.submit(snaps[(b + 1) % 4], wait_us=10_000_000), (b + 1) % 4))
+            if b % 20 == 19:
+                ids.append((srv.submit(snaps[(b + 1) % 4], wait_us=10_000_000), (b + 1) % 4))
+        for k in range(3):  # at the final watermark
+            ids.append((srv.submit(snaps[k + 1], wait_us=10_000_000), k + 1))
         results = [(srv.wait(rid), k) for rid, k in ids]
-    seen = set()
+    seen = []
     for (rec, info), k in results:
         wm = info["watermark"]
         assert w.n_initial <= wm <= final
         off = w.offsets[: wm + 1]
         want = oracle.allf_pairs(off, w.lits[: int(off[-1])], snaps[k])
         assert np.array_equal(gss.expand_reports(rec), want)
-        seen.add(wm)
-    assert len(seen) > 1  # requests saw different database sizes
+        seen.append(wm)
+    assert final == 6_000_000 and seen.count(final) >= 3
+    assert len(set(seen)) >= 4  # requests saw different database sizes

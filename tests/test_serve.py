@@ -235,3 +235,43 @@ def test_serve_result_deadline(work, snaps):
         # a result taken within the deadline is unaffected
         rec, info = srv.wait(srv.submit(snaps[2], wait_us=10_000_000), wait_us=5_000_000)
         np.testing.assert_array_equal(gss.expand_reports(rec), prefix_oracle(work, work.n_initial, snaps[2]))
+
+
+def test_serve_padding_never_counts_against_capacity(work):
+    """Trigger mode, unit clauses, requests of fewer than 32 assignments launched together: the
+    U rows that pad each request's plane word would make every unit clause trigger.  Their
+    records must never be made, so a launch capacity that only those records would exceed does
+    not fail any request, and each result equals the oracle alone and in the mix."""
+    V = work.n_vars
+    n_units = 256
+    rng = np.random.default_rng(11)
+    vs = rng.choice(V, size=n_units, replace=False)
+    lits = (2 * vs + rng.integers(0, 2, size=n_units)).astype(np.uint32)
+    off = np.arange(n_units + 1, dtype=np.uint64)
+    # every real assignment makes every unit literal T, except literal i in request i: one real record each
+    base = np.zeros(V, np.uint8)
+    base[vs] = np.where(lits & 1, 2, 1)  # v = T for literal v, v = F for literal not v
+    reqs = []
+    for i, n in enumerate((1, 3, 7, 12, 20, 31, 2, 5)):
+        codes = np.tile(base, (n, 1))
+        codes[n - 1, vs[i]] = 0  # literal i becomes U in the last row: the unit clause triggers there
+        reqs.append(codes)
+    want = [oracle.trigger_pairs(off, lits, c) for c in reqs]
+    assert all(len(w) == 1 for w in want)
+    with make_server(work, mode=gss.GSS_MODE_TRIGGER, lanes=1, lane_report_capacity=16) as srv:
+        srv.add_clauses(off, lits)
+        alone = [run_alone(srv, c)[0] for c in reqs]
+        batched = False
+        for attempt in range(5):  # back to back: later requests join launches together
+            ids = [srv.submit(c, wait_us=10_000_000) for c in reqs]
+            mixed = [srv.wait(rid) for rid in ids]
+            for (rec, info), w in zip(mixed, want):
+                np.testing.assert_array_equal(gss.expand_reports(rec), w)
+            batched |= max(info["batch_words"] for _, info in mixed) > 1
+            if batched:
+                break
+        st = srv.stats()
+    for a, w in zip(alone, want):
+        np.testing.assert_array_equal(a, w)
+    assert st["completed"] == st["submitted"] and st["reports"] == st["completed"]
+    assert batched, "no launch carried more than one request"
