@@ -9,7 +9,10 @@ test every clause against every assignment, compact the hits into report records
 read back their count.  value = clauses x assignments tested per second (G/s).
 
 e2e: the same step through the public API from pinned HOST memory: the codes go
-host->device inside the timed region and the records come back device->host.
+host->device inside the timed region and the records come back device->host.  The
+context keeps two plane sets, so step k + 1's codes cross the host link while step k's
+test runs; the line also carries the host link's copy rate, measured in the same run, and
+the fraction of the bound it sets that e2e reaches.
 
 --impl reference runs the oracle (plain C on the host cores) on a bounded sample of
 the same workload, the reference arm of this comparison.
@@ -545,6 +548,8 @@ def main():
     ap.add_argument("--serve-tests-in-flight", type=int, default=1)
     ap.add_argument("--mode", default="allf", choices=["allf", "trigger"],
                     help="what a pair reports: all literals F (default) or Definition 'triggers'")
+    ap.add_argument("--overlap", action="store_true",
+                    help="issue step k+1's packing before step k's count is read, beside step k's test")
     ap.add_argument("--layout", default="frequency", choices=["frequency", "identity"],
                     help="internal variable numbering of the clause database")
     args = ap.parse_args()
@@ -585,8 +590,10 @@ def main():
     cap = max(1 << 22, 8 * len(inst.planted) + (16 if args.mode == "trigger" else 4) * m * ((N + 1023) // 1024))
     layout = gss.GSS_LAYOUT_FREQUENCY if args.layout == "frequency" else gss.GSS_LAYOUT_IDENTITY
     mode = gss.GSS_MODE_TRIGGER if args.mode == "trigger" else gss.GSS_MODE_ALLF
+    # two plane sets: the next set can be copied and packed while the last one is tested
+    pack_stream = torch.cuda.Stream()
     ctx = gss.Context(V, device=local, stream=stream, report_capacity=cap, max_assignments=max(N, 32), layout=layout,
-                      mode=mode)
+                      mode=mode, pipeline=2, pack_stream=pack_stream)
 
     # a-1: ingest the database (once; the database stays resident like the paper's GPU clause store)
     torch.cuda.synchronize()
@@ -626,26 +633,47 @@ def main():
         step()
         ctx.report_count()
 
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    start.record(stream)
-    for k in range(args.steps):
-        ev[k][0].record(stream)
-        gss.gss_set_assignments_device(ctx.ptr, d_codes.data_ptr(), pitch, N)
-        ev[k][1].record(stream)
-        ctx.test()
-        ev[k][2].record(stream)
-        ctx.report_count()  # the step's result (record count) read back to the host
-    end.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    elapsed = start.elapsed_time(end) / 1e3
-    t_pack = float(np.mean([e[0].elapsed_time(e[1]) for e in ev])) / 1e3
-    t_test = float(np.mean([e[1].elapsed_time(e[2]) for e in ev])) / 1e3
+    def timed_steps(n_steps: int):
+        """n_steps steps: pack step k's set, test it, read its record count back to the host.
+        Packing and testing take turns (each kernel fills the GPU; running them side by side
+        measured slower); with --overlap, step k + 1's packing is issued before step k's count
+        is read, so that it runs beside step k's test.  Each kernel is bracketed by CUDA events
+        on the stream it runs on (after its wait for the other stream)."""
+        evp = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(n_steps)]
+        evt = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(n_steps)]
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+        def pack(k):
+            evp[k][0].record(pack_stream)
+            gss.gss_set_assignments_device(ctx.ptr, d_codes.data_ptr(), pitch, N)
+            evp[k][1].record(pack_stream)
+
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        start.record(stream)
+        pack_stream.wait_event(start)
+        pack(0)
+        for k in range(n_steps):
+            stream.wait_event(evp[k][1])
+            evt[k][0].record(stream)
+            ctx.test()
+            evt[k][1].record(stream)
+            if args.overlap and k + 1 < n_steps:
+                pack(k + 1)  # runs beside step k's test
+            ctx.report_count()  # step k's result (record count) read back to the host
+            if not args.overlap and k + 1 < n_steps:
+                pack(k + 1)
+        end.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        el = start.elapsed_time(end) / 1e3
+        tp = float(np.mean([e[0].elapsed_time(e[1]) for e in evp])) / 1e3
+        tt = float(np.mean([e[0].elapsed_time(e[1]) for e in evt])) / 1e3
+        return el, tp, tt
+
+    elapsed, t_pack, t_test = timed_steps(args.steps)
     elapsed = max_over_ranks(elapsed, dist)
 
     split = None
@@ -665,12 +693,27 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        ctx.set_assignments(h_codes.numpy())
+    # every step copies its codes in and its records out; with two plane sets the codes of step
+    # k + 1 cross the host link while step k's test runs, before step k's records are read
+    ctx.set_assignments(h_codes.numpy())
+    for k in range(e2e_steps):
         ctx.test()
+        if k + 1 < e2e_steps:
+            ctx.set_assignments(h_codes.numpy())
         ctx.fetch_reports(h_rec)
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s, dist)
+    # the host link measured in the same run: the step's codes, pinned host -> device, one copy
+    link_s = []
+    for _ in range(3):
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            l0.record(stream)
+            d_codes.copy_(h_codes, non_blocking=True)
+            l1.record(stream)
+        l1.synchronize()
+        link_s.append(l0.elapsed_time(l1) / 1e3)
+    link_gbs = N * V / min(link_s) / 1e9
     clk = clocks.stop()
 
     value = whole_job_rate(m * N, world, args.steps, elapsed)
@@ -714,7 +757,11 @@ def main():
                    "parallelism": f"weak x{world}: one clause database per GPU, shared assignment set",
                    "layout": args.layout, "mode": args.mode},
         "e2e": {"value": whole_job_rate(m * N, world, e2e_steps, e2e_s), "unit": UNIT, "h2d_bytes_per_step": N * V,
-                "d2h_bytes_per_step": 12 * n_records + 48},
+                "d2h_bytes_per_step": 12 * n_records + 48,
+                # the bound the host link sets: one step's codes at the measured copy rate
+                "host_link_GBps": link_gbs, "link_cap_value": m * N * world / (N * V / (link_gbs * 1e9)) / 1e9,
+                "frac_of_link_cap": whole_job_rate(m * N, world, e2e_steps, e2e_s) /
+                (m * N * world / (N * V / (link_gbs * 1e9)) / 1e9)},
         "roofline": {k: v for k, v in roof[dominant].items()},
         "roofline_all": roof,
         "kernel_only": {"test_tests_per_s_G": m * N / t_test / 1e9, "pack_us": t_pack * 1e6,

@@ -84,7 +84,25 @@ typedef struct {
   uint32_t mode;             /* GSS_MODE_ALLF (default) or GSS_MODE_TRIGGER */
   uint64_t mem_budget_bytes; /* cap on device bytes the context may hold; 0 = no cap */
   uint32_t layout;           /* GSS_LAYOUT_FREQUENCY (default) or GSS_LAYOUT_IDENTITY */
+  uint32_t pipeline;         /* 1 (default) or 2: see below */
+  void* pack_stream;         /* pipeline 2: cudaStream_t the packing runs on; NULL: the context creates one */
+  uint32_t clauses_per_tile; /* test tile shape: 32 (a lane per clause), 16 (two lanes per clause: its
+                                first 8 and next 8 literals in parallel), or 0 (default: 32, which
+                                measured faster on GB300 for short and long clauses alike) */
 } gss_config;
+
+/*
+ * pipeline = 2 keeps two plane sets.  gss_set_assignments / _device pack the new set on
+ * pack_stream into the plane set the last gss_test does not read, while that test may still
+ * run on `stream`; gss_test waits (on the device) for its set's packing.  So a caller that
+ * issues gss_set_assignments for set k + 1 before it reads the results of set k lets the
+ * next set's host copy and packing proceed while the last test runs.  (On GB300 the packing
+ * and test kernels each fill the GPU: running them side by side was measured slower than
+ * running them in turn, so the gain is in hiding host copies and host round trips.)
+ * Results are the same as with pipeline = 1.  Ordering: packing is not ordered after work
+ * queued on `stream`; device codes written by other work must be complete before the
+ * call (or ordered onto pack_stream by the caller).  Twice the plane memory is held.
+ */
 
 /*
  * One report record: clause `clause_id` passes the test on assignment
@@ -126,14 +144,21 @@ typedef struct {
 int gss_config_init(gss_config* cfg);
 
 /*
- * Create a context for V = n_vars variables (1 <= V < 2^31) on cfg->device.
+ * Create a context for V = n_vars variables (1 <= V < 2^31) on cfg->device:
+ * the GPU-side clause store of Section 3.6 (the GPU keeps every clause the
+ * solver threads export to it) with room for one assignment set of up to
+ * cfg->max_assignments assignments (Section 3.4's bit-packed assignments).
  * cfg may be NULL (defaults).  On success *out owns the device state.
  * Errors: GSS_E_INVAL (bad V, bad config), GSS_E_CUDA (no device / bad
  * stream), GSS_E_NOMEM.
  */
 int gss_create(gss_ctx** out, uint32_t n_vars, const gss_config* cfg);
 
-/* Release every device and host resource of ctx (waits for its queued work). NULL is a no-op. */
+/*
+ * Release every device and host resource of ctx (the clause store and
+ * assignment planes of Sections 3.4 and 3.6); waits for its queued work.
+ * NULL is a no-op.
+ */
 int gss_destroy(gss_ctx* ctx);
 
 /* ------------------------------------------------------------- clauses */
@@ -148,7 +173,10 @@ int gss_destroy(gss_ctx* ctx);
  * All or nothing: on GSS_E_INVAL (empty clause, literal >= 2V, offsets[0]
  * != 0) or GSS_E_NOMEM the database is unchanged.  Synchronises the stream
  * (validation result).  Duplicate literals are allowed; a clause holding
- * l and not l is accepted and is never reported.
+ * l and not l is accepted and is never reported.  With GSS_LAYOUT_FREQUENCY the
+ * first batch fixes the internal variable numbering; an assignment set given
+ * before it is packed again from the same codes (so device codes passed to
+ * gss_set_assignments_device before the first batch must still be valid).
  */
 int gss_add_clauses(gss_ctx* ctx, const uint64_t* offsets, uint64_t n_clauses, const uint32_t* lits,
                     uint32_t* first_id);
@@ -195,8 +223,11 @@ int gss_set_assignments_device(gss_ctx* ctx, const uint8_t* d_values, uint64_t p
 int gss_test(gss_ctx* ctx);
 
 /*
- * Wait for the last gss_test and copy its records to host buffer `out`
- * (capacity `cap` records; out may be NULL when cap is 0).  *n_out receives
+ * Wait for the last gss_test and copy its records to host buffer `out`: the
+ * report(i, mask) calls of Listing multiTrigger (Section 4.3), by which the
+ * GPU tells each solver thread which clauses triggered on its assignments
+ * (Section 3.6).  `out` has capacity `cap` records (out may be NULL when cap
+ * is 0).  *n_out receives
  * the total number of records the test produced.  Returns GSS_E_OVERFLOW if
  * that number exceeds cap (min(cap, n) records written) or the device buffer
  * (the test must then be re-run after gss_set_report_capacity), GSS_E_INVAL
@@ -231,8 +262,9 @@ int gss_set_mode(gss_ctx* ctx, uint32_t mode);
  * then one persistent launch in which warps steal 32-clause tiles of any
  * instance from a device counter.  The graph is captured on the first test
  * and again whenever an instance is added, the mode changes, or an instance's
- * assignment set changes size or source buffer.  The launch shape (tiles per
- * steal, grid) is chosen on the first test by timing candidates on the batch.
+ * assignment set changes size or source buffer.  The launch shape (tile shape:
+ * clauses per warp tile; tiles per steal; grid) is chosen on the first test by
+ * timing candidates on the batch.
  * Instances sharing a batch use the batch's device, stream, mode and layout.
  */
 typedef struct gss_batch gss_batch;
@@ -242,11 +274,13 @@ typedef struct {
   uint32_t n_groups;           /* test launches per run: one per aggregate row width */
   uint32_t tiles_per_steal[3]; /* autotuned, per group */
   uint32_t grid[3];            /* autotuned CTAs, per group */
-  uint64_t n_tiles[3];         /* 32-clause tiles per group */
+  uint64_t n_tiles[3];         /* tiles (of the tuned shape) per group */
   uint64_t runs;               /* gss_batch_test calls */
   float tuned_test_us;         /* test-launch time measured by the autotuner (0 when the choices came
                                   from the cache file named by the environment variable
                                   GSS_AUTOTUNE_CACHE, which keeps them across processes) */
+  uint32_t clauses_per_tile[3];/* autotuned tile shape, per group: 32 (a lane per clause) or 16 (two
+                                  lanes per clause, head0 and head1 tested in parallel) */
 } gss_batch_info;
 
 /* Create an empty batch (cfg: device, stream, mode, layout; the rest is per instance). */
@@ -451,6 +485,9 @@ typedef struct {
   uint64_t expired;                       /* kept results dropped after result_ttl_us */
   uint32_t slots, pad;
   double p50_us, p99_us, max_us, mean_us; /* latency of completed requests */
+  uint64_t next_clause_id;                /* requests admitted now test the resident clauses with
+                                             smaller ids (committed_clauses counts the resident ones) */
+  uint64_t reductions, clauses_removed;   /* gss_server_reduce calls and the clauses they removed */
 } gss_server_stats;
 
 /* Fill *cfg with the defaults: device 0, all-F, frequency layout, 1M clauses and 16M literals
@@ -491,6 +528,35 @@ int gss_server_submit(gss_server* srv, const uint8_t* values, uint32_t n_assign,
  */
 int gss_server_wait(gss_server* srv, uint64_t request_id, int64_t wait_us, gss_report* out, uint64_t cap,
                     uint64_t* n_out, gss_request_info* info);
+
+/*
+ * Clause activity and deletion on the server's resident database (Section 3.6: the GPU
+ * deletes clauses by activity as MiniSat does, bumping a clause whenever it triggers).
+ * gss_server_set_activity switches activities on (decay as gss_set_activity) and reserves
+ * the activity arrays for max_clauses; it needs tests_in_flight = 1, so that one test bumps
+ * at a time (GSS_E_STATE otherwise).  Each launch then counts as one test of gss_set_activity's
+ * rules: every clause reported by the launch (for any of its requests) is bumped once by the
+ * increment, which grows by 1 / decay after each launch; a clause added starts at the
+ * current increment.
+ *
+ * gss_server_reduce removes floor(f * n) of the n resident clauses longer than two literals,
+ * those with the smallest (activity, id), exactly as gss_reduce_db.  It waits until no launch
+ * runs, holds new launches (requests are still admitted) and ingest meanwhile, compacts the
+ * database into new arrays, reserves capacity again and publishes it; launches started
+ * afterwards read the compacted database.  Watermarks are clause-id bounds: a request tests
+ * the clauses resident at its launch whose id is below its watermark, so a request admitted
+ * before a reduction but launched after it skips the removed clauses.  Ids never change and
+ * are never reused.  Needs room for a second copy of the database while it runs; on
+ * GSS_E_NOMEM the database is unchanged.  *n_removed (nullable) receives the count.
+ *
+ * gss_server_get_activity / gss_server_get_clause_ids copy the activities / ids of the
+ * resident clauses in position order (as gss_get_activity / gss_get_clause_ids); values read
+ * while launches run may be mid-update.
+ */
+int gss_server_set_activity(gss_server* srv, float decay);
+int gss_server_reduce(gss_server* srv, double remove_fraction, uint64_t* n_removed);
+int gss_server_get_activity(gss_server* srv, float* out, uint64_t cap, uint64_t* n_out);
+int gss_server_get_clause_ids(gss_server* srv, uint32_t* out, uint64_t cap, uint64_t* n_out);
 
 /* Counters since creation and the latency percentiles of every completed request. */
 int gss_server_get_stats(gss_server* srv, gss_server_stats* out);

@@ -36,7 +36,8 @@ REPORT_DTYPE = np.dtype([("clause_id", "<u4"), ("word", "<u4"), ("mask", "<u4")]
 class gss_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("report_capacity", ctypes.c_uint64),
                 ("max_assignments", ctypes.c_uint32), ("mode", ctypes.c_uint32),
-                ("mem_budget_bytes", ctypes.c_uint64), ("layout", ctypes.c_uint32)]
+                ("mem_budget_bytes", ctypes.c_uint64), ("layout", ctypes.c_uint32), ("pipeline", ctypes.c_uint32),
+                ("pack_stream", ctypes.c_void_p), ("clauses_per_tile", ctypes.c_uint32)]
 
 
 class gss_stats(ctypes.Structure):
@@ -51,7 +52,8 @@ class gss_stats(ctypes.Structure):
 class gss_batch_info(ctypes.Structure):
     _fields_ = [("n_instances", ctypes.c_uint32), ("n_groups", ctypes.c_uint32),
                 ("tiles_per_steal", ctypes.c_uint32 * 3), ("grid", ctypes.c_uint32 * 3),
-                ("n_tiles", ctypes.c_uint64 * 3), ("runs", ctypes.c_uint64), ("tuned_test_us", ctypes.c_float)]
+                ("n_tiles", ctypes.c_uint64 * 3), ("runs", ctypes.c_uint64), ("tuned_test_us", ctypes.c_float),
+                ("clauses_per_tile", ctypes.c_uint32 * 3)]
 
 
 class gss_server_config(ctypes.Structure):
@@ -74,7 +76,8 @@ class gss_server_stats(ctypes.Structure):
                 ("reports", ctypes.c_uint64), ("committed_clauses", ctypes.c_uint64), ("expired", ctypes.c_uint64),
                 ("slots", ctypes.c_uint32),
                 ("pad", ctypes.c_uint32), ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
-                ("max_us", ctypes.c_double), ("mean_us", ctypes.c_double)]
+                ("max_us", ctypes.c_double), ("mean_us", ctypes.c_double), ("next_clause_id", ctypes.c_uint64),
+                ("reductions", ctypes.c_uint64), ("clauses_removed", ctypes.c_uint64)]
 
 
 class GssError(RuntimeError):
@@ -132,6 +135,10 @@ SIGNATURES = {
     "gss_server_wait": (i32, [P, u64, ctypes.c_int64, P, u64, P, P]),
     "gss_server_get_stats": (i32, [P, P]),
     "gss_server_last_error": (ctypes.c_char_p, [P]),
+    "gss_server_set_activity": (i32, [P, ctypes.c_float]),
+    "gss_server_reduce": (i32, [P, ctypes.c_double, P]),
+    "gss_server_get_activity": (i32, [P, P, u64, P]),
+    "gss_server_get_clause_ids": (i32, [P, P, u64, P]),
 }
 
 
@@ -296,10 +303,15 @@ class Context:
 
     def __init__(self, n_vars: int, device: int = 0, stream=None, report_capacity: int = 1 << 22,
                  max_assignments: int = 1024, mode: int = GSS_MODE_ALLF, mem_budget_bytes: int = 0,
-                 layout: int = GSS_LAYOUT_FREQUENCY):
+                 layout: int = GSS_LAYOUT_FREQUENCY, pipeline: int = 1, pack_stream=None,
+                 clauses_per_tile: int = 0):
         cfg = gss_config_init()
         cfg.device = device
         cfg.stream = ctypes.c_void_p(_stream_handle(stream)) if stream is not None else None
+        cfg.pipeline = pipeline
+        cfg.clauses_per_tile = clauses_per_tile
+        cfg.pack_stream = ctypes.c_void_p(_stream_handle(pack_stream)) if pack_stream is not None else None
+        self._pack_stream = pack_stream
         cfg.report_capacity = report_capacity
         cfg.max_assignments = max_assignments
         cfg.mode = mode
@@ -504,7 +516,7 @@ class Batch:
         k = x.n_groups
         return {"n_instances": x.n_instances, "n_groups": k, "tiles_per_steal": list(x.tiles_per_steal)[:k],
                 "grid": list(x.grid)[:k], "n_tiles": list(x.n_tiles)[:k], "runs": x.runs,
-                "tuned_test_us": x.tuned_test_us}
+                "tuned_test_us": x.tuned_test_us, "clauses_per_tile": list(x.clauses_per_tile)[:k]}
 
 
 # ---------------------------------------------------------------- serving
@@ -599,3 +611,28 @@ class Server:
         x = gss_server_stats()
         self._check(load().gss_server_get_stats(self.ptr, ctypes.byref(x)))
         return {k: getattr(x, k) for k, _ in x._fields_ if k != "pad"}
+
+    def set_activity(self, decay: float) -> None:
+        self._check(load().gss_server_set_activity(self.ptr, decay))
+
+    def reduce(self, remove_fraction: float) -> int:
+        n = ctypes.c_uint64()
+        self._check(load().gss_server_reduce(self.ptr, remove_fraction, ctypes.byref(n)))
+        return n.value
+
+    def _per_clause(self, fn, dtype) -> np.ndarray:
+        n = ctypes.c_uint64()
+        rc = fn(self.ptr, None, 0, ctypes.byref(n))
+        if rc not in (GSS_OK, GSS_E_OVERFLOW):
+            self._check(rc)
+        out = np.empty(n.value, dtype)
+        self._check(fn(self.ptr, ctypes.c_void_p(out.ctypes.data), len(out), ctypes.byref(n)))
+        return out
+
+    def activity(self) -> np.ndarray:
+        """Activities of the resident clauses, in position order."""
+        return self._per_clause(load().gss_server_get_activity, np.float32)
+
+    def clause_ids(self) -> np.ndarray:
+        """Ids of the resident clauses, in position order."""
+        return self._per_clause(load().gss_server_get_clause_ids, np.uint32)

@@ -6,6 +6,7 @@
 // this file only sizes buffers, copies host data in and out, and launches.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
@@ -123,50 +124,76 @@ uint32_t words_stride(uint32_t N) {  // plane row stride in 32-bit words: a powe
 
 uint32_t agg_stride(uint32_t Wp) { return Wp <= 32 ? 1 : Wp / 32; }  // 1, 2, 4, ... 32 words
 
-int ensure_planes(gss_ctx* c) {  // allocates what is missing, so a call after a failed one completes the set
+// Point the latest-set aliases (P, aggF, ...) at plane set b.
+void use_set(gss_ctx* c, uint32_t b) {
+  c->cur = b;
+  c->P = c->sets[b].P;
+  c->aggF = c->sets[b].aggF;
+  c->aggU = c->sets[b].aggU;
+  c->agg2F = c->sets[b].agg2F;
+  c->agg2U = c->sets[b].agg2U;
+}
+
+int ensure_planes(gss_ctx* c) {  // allocates what is missing, so a call after a failed one completes the sets
   const uint32_t Wp = words_stride(c->max_N), AWp = agg_stride(Wp);
   int rc;
   void* p;
-  if (!c->P) {
-    if ((rc = dev_alloc(c, &p, (2ull * c->V + 2) * Wp * 4))) return rc;
-    c->P = static_cast<uint32_t*>(p);
+  for (uint32_t b = 0; b < c->pipeline; ++b) {
+    gss_ctx::PlaneSet& q = c->sets[b];
+    if (!q.P) {
+      if ((rc = dev_alloc(c, &p, (2ull * c->V + 2) * Wp * 4))) return rc;
+      q.P = static_cast<uint32_t*>(p);
+    }
+    if (!q.aggF) {
+      if ((rc = dev_alloc(c, &p, (2ull * c->V + 2) * AWp * 4))) return rc;
+      q.aggF = static_cast<uint32_t*>(p);
+    }
+    if (!q.aggU) {
+      if ((rc = dev_alloc(c, &p, (c->V + 1ull) * AWp * 4))) return rc;
+      q.aggU = static_cast<uint32_t*>(p);
+    }
+    if (AWp > 4 && !q.agg2F) {
+      if ((rc = dev_alloc(c, &p, (2ull * c->V + 2) * 4))) return rc;
+      q.agg2F = static_cast<uint32_t*>(p);
+    }
+    if (AWp > 4 && !q.agg2U) {
+      if ((rc = dev_alloc(c, &p, (c->V + 1ull) * 4))) return rc;
+      q.agg2U = static_cast<uint32_t*>(p);
+    }
   }
-  if (!c->aggF) {
-    if ((rc = dev_alloc(c, &p, (2ull * c->V + 2) * AWp * 4))) return rc;
-    c->aggF = static_cast<uint32_t*>(p);
-  }
-  if (!c->aggU) {
-    if ((rc = dev_alloc(c, &p, (c->V + 1ull) * AWp * 4))) return rc;
-    c->aggU = static_cast<uint32_t*>(p);
-  }
-  if (AWp > 4 && !c->agg2F) {
-    if ((rc = dev_alloc(c, &p, (2ull * c->V + 2) * 4))) return rc;
-    c->agg2F = static_cast<uint32_t*>(p);
-  }
-  if (AWp > 4 && !c->agg2U) {
-    if ((rc = dev_alloc(c, &p, (c->V + 1ull) * 4))) return rc;
-    c->agg2U = static_cast<uint32_t*>(p);
-  }
+  use_set(c, c->cur);
   return GSS_OK;
 }
 
+// Read the ingest status and the status of the plane set the last test read (the other
+// set's may be in the middle of a packing on pack_stream).
 int sync_status(gss_ctx* c) {
-  CK(c, cudaMemcpyAsync(c->h_st, c->st, 2 * sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
+  const uint32_t i = set_status_index(c->tested_set);
+  CK(c, cudaMemcpyAsync(c->h_st + 1, c->st + 1, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaMemcpyAsync(c->h_st + i, c->st + i, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   return GSS_OK;
 }
 
-int launch_grid(gss_ctx* c, int mode, uint32_t AWp) {
+int launch_grid(gss_ctx* c, int mode, uint32_t AWp, int cpw) {
   const bool wide = AWp > 4;
-  int& g = wide ? c->grid_wide[mode] : c->grid[mode][AWp];
-  if (!g) g = test_grid_size(mode, AWp, c->n_sms, wide);
+  int& g = wide ? c->grid_wide[mode] : c->grid[mode][AWp][cpw == 16 ? 1 : 0];
+  if (!g) g = test_grid_size(mode, AWp, c->n_sms, wide, cpw);
   return g;
 }
 
 void release(gss_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->pack_stream && c->pack_stream != c->stream) cudaStreamSynchronize(c->pack_stream);
   while (!c->allocs.empty()) dev_free(c, c->allocs.begin()->first);
   if (c->h_st) cudaFreeHost(c->h_st);
+  for (int b = 0; b < 2; ++b) {
+    if (c->ev_packed[b]) cudaEventDestroy(c->ev_packed[b]);
+    if (c->ev_tested[b]) cudaEventDestroy(c->ev_tested[b]);
+  }
+  if (c->ev_copied) cudaEventDestroy(c->ev_copied);
+
+  if (c->own_pack_stream && c->pack_stream) cudaStreamDestroy(c->pack_stream);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -185,6 +212,9 @@ int gss_config_init(gss_config* cfg) {
   cfg->mode = GSS_MODE_ALLF;
   cfg->mem_budget_bytes = 0;
   cfg->layout = GSS_LAYOUT_FREQUENCY;
+  cfg->pipeline = 1;
+  cfg->pack_stream = nullptr;
+  cfg->clauses_per_tile = 0;
   return GSS_OK;
 }
 
@@ -197,6 +227,8 @@ int gss_create(gss_ctx** out, uint32_t n_vars, const gss_config* cfg_in) {
   if (cfg.max_assignments == 0 || cfg.max_assignments > GSS_MAX_ASSIGNMENTS) return GSS_E_INVAL;
   if (cfg.mode != GSS_MODE_ALLF && cfg.mode != GSS_MODE_TRIGGER) return GSS_E_INVAL;
   if (cfg.layout != GSS_LAYOUT_IDENTITY && cfg.layout != GSS_LAYOUT_FREQUENCY) return GSS_E_INVAL;
+  if (cfg.pipeline != 1 && cfg.pipeline != 2) return GSS_E_INVAL;
+  if (cfg.clauses_per_tile != 0 && cfg.clauses_per_tile != 16 && cfg.clauses_per_tile != 32) return GSS_E_INVAL;
   int n_dev = 0;
   if (cudaGetDeviceCount(&n_dev) != cudaSuccess || cfg.device < 0 || cfg.device >= n_dev) {
     cudaGetLastError();
@@ -222,13 +254,32 @@ int gss_create(gss_ctx** out, uint32_t n_vars, const gss_config* cfg_in) {
   } else {
     c->own_stream = true;
   }
+  c->pipeline = cfg.pipeline;
+  c->tile_clauses = cfg.clauses_per_tile;
+  c->pack_stream = c->stream;
+  if (c->pipeline == 2) {
+    if (cfg.pack_stream) {
+      c->pack_stream = static_cast<cudaStream_t>(cfg.pack_stream);
+    } else if (cudaStreamCreateWithFlags(&c->pack_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      c->pack_stream = nullptr;
+      rc = GSS_E_CUDA;
+    } else {
+      c->own_pack_stream = true;
+    }
+    for (int b = 0; b < 2 && !rc; ++b)
+      if (cudaEventCreateWithFlags(&c->ev_packed[b], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c->ev_tested[b], cudaEventDisableTiming) != cudaSuccess)
+        rc = GSS_E_CUDA;
+  }
+  if (!rc && cudaEventCreateWithFlags(&c->ev_copied, cudaEventDisableTiming) != cudaSuccess) rc = GSS_E_CUDA;
+
   void* p = nullptr;
-  if (cudaMallocHost(&p, 2 * sizeof(DevStatus)) != cudaSuccess) rc = GSS_E_NOMEM;
+  if (!rc && cudaMallocHost(&p, 3 * sizeof(DevStatus)) != cudaSuccess) rc = GSS_E_NOMEM;
   c->h_st = static_cast<DevStatus*>(p);
-  if (!rc) rc = dev_alloc(c, &p, 2 * sizeof(DevStatus));
+  if (!rc) rc = dev_alloc(c, &p, 3 * sizeof(DevStatus));
   if (!rc) {
     c->st = static_cast<DevStatus*>(p);
-    if (cudaMemsetAsync(c->st, 0, 2 * sizeof(DevStatus), c->stream) != cudaSuccess) rc = GSS_E_CUDA;
+    if (cudaMemsetAsync(c->st, 0, 3 * sizeof(DevStatus), c->stream) != cudaSuccess) rc = GSS_E_CUDA;
   }
   if (!rc) {
     c->rec_cap = cfg.report_capacity ? cfg.report_capacity : 1;
@@ -307,6 +358,10 @@ int gss_add_clauses(gss_ctx* c, const uint64_t* offsets, uint64_t n, const uint3
       return fail(c, GSS_E_CUDA, "variable ranking: %s", cudaGetErrorString(e));
     }
     c->map = static_cast<uint32_t*>(pm);
+    if (c->have_assign && c->N) {  // a set packed before the numbering existed: pack it again in the numbering
+      c->pack_set = c->cur;
+      if ((rc = pack_staged(c, c->pack_stream))) return rc;
+    }
   }
   if (c->map) CK(c, launch_translate(blits, L, c->map, c->stream));
   CK(c, launch_build_heads(c->boff, n, c->L, c->head0 + c->m * 8, c->head1 + c->m * 8, c->lits, c->V, c->stream));
@@ -347,9 +402,13 @@ int stage_assignments(gss_ctx* c, const uint8_t* src, uint64_t pitch, uint32_t n
   DeviceGuard dg(c->device);
   int rc;
   if ((rc = ensure_planes(c))) return rc;
+  // pipeline 2: the set the last test did not read; packing waits for the last test that read it
+  const uint32_t b = c->pipeline == 2 ? (c->cur ^ 1u) : 0u;
+  cudaStream_t ps = c->pack_stream;
   c->have_assign = false;
-  c->tested = false;
-  CK(c, cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream));
+  if (b == c->tested_set) c->tested = false;  // its status words are reset below: the last test's results go
+  if (c->pipeline == 2) CK(c, cudaStreamWaitEvent(ps, c->ev_tested[b], 0));
+  CK(c, cudaMemsetAsync(set_status(c, b), 0, sizeof(DevStatus), ps));
   const uint32_t Wp = words_stride(n ? n : 1);
   const uint32_t AWp = agg_stride(Wp);
   const uint8_t* codes = src;
@@ -358,6 +417,7 @@ int stage_assignments(gss_ctx* c, const uint8_t* src, uint64_t pitch, uint32_t n
   const bool aligned = device_src && pitch % 16 == 0 && (reinterpret_cast<uintptr_t>(src) % 16) == 0;
   if (n && !aligned) {  // host data, or a device layout the packing kernel cannot read as 32-bit words
     if (c->codes_rows < n) {
+      CK(c, cudaStreamSynchronize(ps));  // a packing of the other set may still read the old buffer
       dev_free(c, c->codes);
       c->codes = nullptr;
       c->codes_rows = 0;
@@ -365,26 +425,38 @@ int stage_assignments(gss_ctx* c, const uint8_t* src, uint64_t pitch, uint32_t n
       if ((rc = dev_alloc(c, &p, (uint64_t)c->max_N * c->Vp))) return rc;
       c->codes = static_cast<uint8_t*>(p);
       c->codes_rows = c->max_N;
-      CK(c, cudaMemsetAsync(c->codes, 0, (uint64_t)c->max_N * c->Vp, c->stream));  // padding columns stay U
+      CK(c, cudaMemsetAsync(c->codes, 0, (uint64_t)c->max_N * c->Vp, ps));  // padding columns stay U
     }
+    // queued on the packing stream: a packing still reading the staging buffer finishes first
     CK(c, cudaMemcpy2DAsync(c->codes, c->Vp, src, device_src ? pitch : c->V, c->V, n,
-                            device_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+                            device_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ps));
+    if (!device_src) {  // the caller may reuse its host buffer once this call returns
+      CK(c, cudaEventRecord(c->ev_copied, ps));
+      CK(c, cudaEventSynchronize(c->ev_copied));
+    }
     codes = c->codes;
     cpitch = c->Vp;
   }
   c->pack_src = codes;
   c->pack_pitch = cpitch;
+  c->pack_set = b;
+  c->sets[b].N = n;
   c->N = n;
   c->Wp = Wp;
   c->AWp = AWp;
+  use_set(c, b);
   c->have_assign = true;
   return GSS_OK;
 }
 
 int pack_staged(gss_ctx* c, cudaStream_t s) {
-  if (c->N) CK(c, launch_pack(c->pack_src, c->pack_pitch, c->V, c->N, c->Wp, c->AWp, c->map, c->P, c->aggF, c->aggU,
-                              c->st, s));
-  if (c->N && c->AWp > 4) CK(c, launch_agg2(c->aggF, c->aggU, c->V, c->AWp, c->agg2F, c->agg2U, s));
+  const uint32_t b = c->pack_set;
+  const gss_ctx::PlaneSet& q = c->sets[b];
+  DevStatus* st = set_status(c, b);
+  if (c->N) CK(c, launch_pack(c->pack_src, c->pack_pitch, c->V, c->N, c->Wp, c->AWp, c->map, q.P, q.aggF, q.aggU, st,
+                              s));
+  if (c->N && c->AWp > 4) CK(c, launch_agg2(q.aggF, q.aggU, c->V, c->AWp, q.agg2F, q.agg2U, s));
+  if (c->pipeline == 2) CK(c, cudaEventRecord(c->ev_packed[b], s));
   return GSS_OK;
 }
 }  // namespace host
@@ -397,7 +469,7 @@ static int set_assignments_common(gss_ctx* c, const uint8_t* src, uint64_t pitch
   int rc = stage_assignments(c, src, pitch, n, device_src);
   if (rc) return rc;
   DeviceGuard dg(c->device);
-  return pack_staged(c, c->stream);
+  return pack_staged(c, c->pack_stream);
 }
 
 int gss_set_assignments(gss_ctx* c, const uint8_t* values, uint32_t n_assign) {
@@ -414,8 +486,11 @@ int gss_test(gss_ctx* c) {
   c->err.clear();
   if (!c->have_assign) return fail(c, GSS_E_STATE, "gss_test before gss_set_assignments");
   DeviceGuard dg(c->device);
-  CK(c, cudaMemsetAsync(&c->st->n_records, 0, 2 * sizeof(unsigned long long), c->stream));  // records, candidates
-  CK(c, cudaMemsetAsync(&c->st->n_super, 0, sizeof(unsigned long long), c->stream));
+  const uint32_t b = c->cur;
+  DevStatus* st = set_status(c, b);
+  if (c->pipeline == 2) CK(c, cudaStreamWaitEvent(c->stream, c->ev_packed[b], 0));  // the set's packing
+  CK(c, cudaMemsetAsync(&st->n_records, 0, 2 * sizeof(unsigned long long), c->stream));  // records, candidates
+  CK(c, cudaMemsetAsync(&st->n_super, 0, sizeof(unsigned long long), c->stream));
   if (c->m && c->N) {
     ClauseView db{c->off, c->lits, c->head0, c->head1, 2u * c->V, c->ext};
     PlaneView pv{c->P, c->aggF, c->aggU, c->Wp, c->AWp, c->N, c->V};
@@ -426,9 +501,13 @@ int gss_test(gss_ctx* c) {
     }
     ActivityView av;
     if (c->act) av = ActivityView{c->act, c->stamp, c->epoch, c->inc};
-    CK(c, launch_test((int)c->mode, db, 0, c->m, pv, c->rec, c->rec_cap, c->st, launch_grid(c, c->mode, c->AWp),
-                      c->stream, nullptr, 0, av, wv));
+    const int cpw = c->tile_clauses ? (int)c->tile_clauses : test_tile_shape(c->m, c->L);
+    CK(c, launch_test((int)c->mode, db, 0, c->m, pv, c->rec, c->rec_cap, st, launch_grid(c, c->mode, c->AWp, cpw),
+                      c->stream, nullptr, 0, av, wv, cpw));
   }
+  if (c->pipeline == 2) CK(c, cudaEventRecord(c->ev_tested[b], c->stream));  // set b may be packed again after this
+  c->tested_set = b;
+  c->tested_N = c->N;
   if (c->act) {  // after the test's bumps: the increment grows by 1 / decay, rescaled past 1e20
     c->epoch = c->epoch + 1 == 0xFFFFFFFFu ? 0 : c->epoch + 1;
     c->inc = c->inc * c->inv_decay;
@@ -452,15 +531,16 @@ int wait_test(gss_ctx* c, uint64_t* n, bool sync) {
   if (!c->tested) return fail(c, GSS_E_STATE, "no gss_test to fetch");
   int rc = sync ? sync_status(c) : GSS_OK;
   if (rc) return rc;
-  if (c->h_st[0].bad_code) {
+  const DevStatus& h = c->h_st[set_status_index(c->tested_set)];
+  if (h.bad_code) {
     *n = 0;
     return fail(c, GSS_E_INVAL, "assignment value code outside {0 = U, 1 = T, 2 = F}");
   }
-  if (c->h_st[0].timeout) {
+  if (h.timeout) {
     *n = 0;
     return fail(c, GSS_E_TIMEOUT, "a bounded device wait gave up; the records of this test are incomplete");
   }
-  *n = c->h_st[0].n_records;
+  *n = h.n_records;
   if (!c->counted) {
     c->counted = true;
     c->records += *n;
@@ -564,13 +644,14 @@ int gss_get_stats(const gss_ctx* c, gss_stats* o) {
   o->report_capacity = c->rec_cap;
   o->tests_run = c->tests_run;
   o->pair_tests = c->pair_tests;
-  o->candidate_pairs = c->tested ? c->h_st[0].n_candidates : 0;
-  o->super_pairs = c->tested ? c->h_st[0].n_super : 0;
+  const DevStatus& h = c->h_st[set_status_index(c->tested_set)];
+  o->candidate_pairs = c->tested ? h.n_candidates : 0;
+  o->super_pairs = c->tested ? h.n_super : 0;
   o->clauses_removed = c->removed;
   o->records = c->records;
   o->overflows = c->overflows;
   o->next_clause_id = c->next_id;
-  o->group_pairs = c->tested ? c->m * (uint64_t)((c->N + 31) / 32) : 0;
+  o->group_pairs = c->tested ? c->m * (uint64_t)((c->tested_N + 31) / 32) : 0;
   return GSS_OK;
 }
 

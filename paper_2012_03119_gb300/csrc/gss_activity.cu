@@ -49,7 +49,38 @@ int alloc(gss_ctx* c, T*& p, uint64_t n) {
   return rc;
 }
 
+// Grow p (capacity cap elements, the first `used` kept) to n elements.
+template <class T>
+int reserve_array(gss_ctx* c, T*& p, uint64_t& cap, uint64_t used, uint64_t n) {
+  if (!p || cap >= n) return GSS_OK;
+  T* q = nullptr;
+  int rc = alloc(c, q, n);
+  if (rc) return rc;
+  cudaError_t e = used ? cudaMemcpyAsync(q, p, used * sizeof(T), cudaMemcpyDeviceToDevice, c->stream) : cudaSuccess;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    dev_free(c, q);
+    return fail(c, GSS_E_CUDA, "reserve: %s", cudaGetErrorString(e));
+  }
+  dev_free(c, p);
+  p = q;
+  cap = n;
+  return GSS_OK;
+}
+
 }  // namespace
+
+namespace gss {
+namespace host {
+int reserve_clause_arrays(gss_ctx* c, uint64_t max_clauses) {
+  Guard g(c->device);
+  int rc;
+  if ((rc = reserve_array(c, c->act, c->cap_act, c->m, max_clauses))) return rc;
+  if ((rc = reserve_array(c, c->stamp, c->cap_stamp, c->m, max_clauses))) return rc;
+  return reserve_array(c, c->ext, c->cap_ext, c->m, max_clauses);
+}
+}  // namespace host
+}  // namespace gss
 
 extern "C" {
 

@@ -7,9 +7,10 @@
 //   2. pack every instance's assignment set (one packing kernel per instance, on parallel
 //      branches of the graph so small instances run side by side);
 //   3. test every clause of every instance in ONE persistent launch per row width (AWp)
-//      in which warps steal 32-clause tiles from a device counter (k_test_batch).
-// The launch shape of step 3 (tiles per steal, grid size) is chosen by timing candidates
-// on the batch itself the first time it runs (gss_batch_get_tuning reports the choice).
+//      in which warps steal clause tiles from a device counter (k_test_batch).
+// The launch shape of step 3 (tile shape -- 32 clauses per warp tile with a lane each, or 16
+// with two lanes each --, tiles per steal, grid size) is chosen by timing candidates on the
+// batch itself the first time it runs (gss_batch_get_info reports the choice).
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -33,14 +34,19 @@ namespace {
 
 constexpr int SIDE_STREAMS = 8;
 
+constexpr int SHAPES = 2;  // tile shapes: index 0 = 32 clauses per tile, 1 = 16 (two lanes per clause)
+inline int shape_cpw(int k) { return k ? 16 : 32; }
+
 struct Group {  // instances sharing one aggregate row width
   uint32_t awp = 1;
   std::vector<uint32_t> members;
-  uint64_t n_tiles = 0;
-  BatchInst* d_inst = nullptr;
+  uint64_t n_tiles[SHAPES] = {0, 0};     // tiles of each shape
+  BatchInst* d_inst[SHAPES] = {nullptr, nullptr};  // descriptors, tile0 counted in tiles of each shape
+  int full_grid[SHAPES] = {0, 0};        // occupancy-derived persistent grid of each shape
   unsigned long long* work = nullptr;
   uint32_t grab = 4;
   int grid = 0;
+  int shape = 0;  // tuned shape
 };
 
 struct Captured {  // what the graph baked in for one instance
@@ -111,7 +117,8 @@ void drop_graph(gss_batch* b) {
 
 void drop_groups(gss_batch* b) {
   for (Group& g : b->groups) {
-    if (g.d_inst) cudaFree(g.d_inst);
+    for (int k = 0; k < SHAPES; ++k)
+      if (g.d_inst[k]) cudaFree(g.d_inst[k]);
     if (g.work) cudaFree(g.work);
   }
   b->groups.clear();
@@ -136,26 +143,31 @@ int build_groups(gss_batch* b) {
     g->members.push_back(i);
   }
   for (Group& g : b->groups) {
-    std::vector<BatchInst> h;
-    uint64_t tiles = 0;
-    for (uint32_t i : g.members) {
-      gss_ctx* c = b->inst[i];
-      BatchInst d{};
-      d.db = ClauseView{c->off, c->lits, c->head0, c->head1, 2u * c->V};
-      d.pv = PlaneView{c->P, c->aggF, c->aggU, c->Wp, c->AWp, c->N, c->V};
-      d.m = c->N ? c->m : 0;  // an empty assignment set has nothing to test
-      d.tile0 = tiles;
-      d.rec = c->rec;
-      d.cap = c->rec_cap;
-      d.st = c->st;
-      tiles += (d.m + 31) / 32;
-      h.push_back(d);
+    for (int k = 0; k < SHAPES; ++k) {
+      const uint64_t cpw = (uint64_t)shape_cpw(k);
+      std::vector<BatchInst> h;
+      uint64_t tiles = 0;
+      for (uint32_t i : g.members) {
+        gss_ctx* c = b->inst[i];
+        BatchInst d{};
+        d.db = ClauseView{c->off, c->lits, c->head0, c->head1, 2u * c->V};
+        d.pv = PlaneView{c->P, c->aggF, c->aggU, c->Wp, c->AWp, c->N, c->V};
+        d.m = c->N ? c->m : 0;  // an empty assignment set has nothing to test
+        d.tile0 = tiles;
+        d.rec = c->rec;
+        d.cap = c->rec_cap;
+        d.st = c->st;
+        tiles += (d.m + cpw - 1) / cpw;
+        h.push_back(d);
+      }
+      g.n_tiles[k] = tiles;
+      BCK(b, cudaMalloc(&g.d_inst[k], h.size() * sizeof(BatchInst)));
+      BCK(b, cudaMemcpyAsync(g.d_inst[k], h.data(), h.size() * sizeof(BatchInst), cudaMemcpyHostToDevice, b->stream));
+      g.full_grid[k] = test_batch_grid_size((int)b->mode, g.awp, (int)cpw, b->n_sms);
     }
-    g.n_tiles = tiles;
-    BCK(b, cudaMalloc(&g.d_inst, h.size() * sizeof(BatchInst)));
     BCK(b, cudaMalloc(&g.work, sizeof(unsigned long long)));
-    BCK(b, cudaMemcpyAsync(g.d_inst, h.data(), h.size() * sizeof(BatchInst), cudaMemcpyHostToDevice, b->stream));
-    g.grid = test_batch_grid_size((int)b->mode, g.awp, b->n_sms);
+    g.shape = 0;
+    g.grid = g.full_grid[0];
   }
   BCK(b, cudaStreamSynchronize(b->stream));
   return GSS_OK;
@@ -163,14 +175,14 @@ int build_groups(gss_batch* b) {
 
 int enqueue_resets(gss_batch* b, cudaStream_t s) {
   for (Group& g : b->groups)
-    BCK(b, launch_batch_reset(g.d_inst, (uint32_t)g.members.size(), g.work, b->bst, s));
+    BCK(b, launch_batch_reset(g.d_inst[0], (uint32_t)g.members.size(), g.work, b->bst, s));
   return GSS_OK;
 }
 
 int enqueue_tests(gss_batch* b, cudaStream_t s) {
   for (Group& g : b->groups)
-    BCK(b, launch_test_batch((int)b->mode, g.awp, g.d_inst, (uint32_t)g.members.size(), g.n_tiles, g.work, g.grab,
-                             b->bst, g.grid, s));
+    BCK(b, launch_test_batch((int)b->mode, g.awp, shape_cpw(g.shape), g.d_inst[g.shape], (uint32_t)g.members.size(),
+                             g.n_tiles[g.shape], g.work, g.grab, b->bst, g.grid, s));
   return GSS_OK;
 }
 
@@ -189,37 +201,52 @@ int enqueue_packs(gss_batch* b) {  // on the side streams, forked from and joine
 }
 
 // Tuned choices can persist across processes: with GSS_AUTOTUNE_CACHE naming a file, each
-// group's (tiles per steal, grid) is stored under a key of the device, the mode, the row
-// width and the octave of the group's tile count, and reused by later runs.
+// group's (tiles per steal, grid, clauses per tile) is stored under a key of the device, the
+// mode, the row width and the octave of the group's tile count, and reused by later runs.
 std::mutex g_cache_mutex;
 
 std::string cache_key(const gss_batch* b, const Group& g) {
   cudaDeviceProp p{};
   cudaGetDeviceProperties(&p, b->device);
   uint32_t oct = 0;
-  while ((g.n_tiles >> oct) > 1) ++oct;
+  while ((g.n_tiles[0] >> oct) > 1) ++oct;
   std::ostringstream k;
   for (const char* c = p.name; *c; ++c) k << (*c == ' ' ? '_' : *c);
   k << "/sm" << b->n_sms << "/mode" << b->mode << "/awp" << g.awp << "/oct" << oct;
   return k.str();
 }
 
-std::map<std::string, std::pair<uint32_t, int>> read_cache(const char* path) {
-  std::map<std::string, std::pair<uint32_t, int>> m;
+struct Choice {
+  uint32_t grab;
+  int grid;
+  int cpw;
+};
+
+std::map<std::string, Choice> read_cache(const char* path) {
+  std::map<std::string, Choice> m;
   std::ifstream f(path);
   std::string key;
   uint32_t grab;
-  int grid;
-  while (f >> key >> grab >> grid)
-    if (grab >= 1 && grab <= 64 && grid >= 1) m[key] = {grab, grid};
+  int grid, cpw;
+  while (f >> key >> grab >> grid >> cpw)
+    if (grab >= 1 && grab <= 64 && grid >= 1 && (cpw == 16 || cpw == 32)) m[key] = Choice{grab, grid, cpw};
   return m;
 }
 
-// Time (tiles per steal, grid) candidates for each group's test launch; keep the fastest.
+// CUDA events that are destroyed on every way out of the autotuner.
+struct EventPair {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ~EventPair() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+};
+
+// Time (tile shape, tiles per steal, grid) candidates for each group's test launch; keep the fastest.
 int autotune(gss_batch* b) {
   int rc;
   const char* cache_path = getenv("GSS_AUTOTUNE_CACHE");
-  std::map<std::string, std::pair<uint32_t, int>> cache;
+  std::map<std::string, Choice> cache;
   if (cache_path && *cache_path) {
     std::lock_guard<std::mutex> lk(g_cache_mutex);
     cache = read_cache(cache_path);
@@ -228,58 +255,62 @@ int autotune(gss_batch* b) {
   for (const Group& g : b->groups) all_cached = all_cached && cache.count(cache_key(b, g)) > 0;
   if (all_cached) {  // earlier runs tuned every group of this shape
     for (Group& g : b->groups) {
-      const auto& v = cache[cache_key(b, g)];
-      g.grab = v.first;
-      g.grid = v.second < g.grid ? v.second : g.grid;
+      const Choice& v = cache[cache_key(b, g)];
+      g.shape = v.cpw == 16 ? 1 : 0;
+      g.grab = v.grab;
+      g.grid = v.grid < g.full_grid[g.shape] ? v.grid : g.full_grid[g.shape];
     }
     b->tuned_us = 0.f;
     b->tuned = true;
     return GSS_OK;
   }
   if ((rc = enqueue_resets(b, b->stream)) || (rc = enqueue_packs(b))) return rc;
-  cudaEvent_t e0, e1;
-  BCK(b, cudaEventCreate(&e0));
-  BCK(b, cudaEventCreate(&e1));
+  EventPair ev;
+  BCK(b, cudaEventCreate(&ev.e0));
+  BCK(b, cudaEventCreate(&ev.e1));
   float total = 0.f;
   for (Group& g : b->groups) {
-    const int full = g.grid;
-    const uint32_t grabs[] = {1, 2, 4, 8, 16};
-    const int grids[] = {full, full / 2 > 0 ? full / 2 : 1};
     float best = 1e30f;
     uint32_t best_grab = 4;
-    int best_grid = full;
-    for (int gd : grids)
-      for (uint32_t gr : grabs) {
-        float ms_min = 1e30f;
-        for (int rep = 0; rep < 3; ++rep) {
-          BCK(b, launch_batch_reset(g.d_inst, (uint32_t)g.members.size(), g.work, b->bst, b->stream));
-          BCK(b, cudaEventRecord(e0, b->stream));
-          BCK(b, launch_test_batch((int)b->mode, g.awp, g.d_inst, (uint32_t)g.members.size(), g.n_tiles, g.work, gr,
-                                   b->bst, gd, b->stream));
-          BCK(b, cudaEventRecord(e1, b->stream));
-          BCK(b, cudaEventSynchronize(e1));
-          float ms = 0.f;
-          BCK(b, cudaEventElapsedTime(&ms, e0, e1));
-          if (ms < ms_min) ms_min = ms;
+    int best_grid = g.full_grid[0], best_shape = 0;
+    for (int k = 0; k < SHAPES; ++k) {
+      const int full = g.full_grid[k];
+      const uint32_t grabs[] = {1, 2, 4, 8, 16};
+      const int grids[] = {full, full / 2 > 0 ? full / 2 : 1};
+      for (int gd : grids)
+        for (uint32_t gr : grabs) {
+          float ms_min = 1e30f;
+          for (int rep = 0; rep < 3; ++rep) {
+            BCK(b, launch_batch_reset(g.d_inst[k], (uint32_t)g.members.size(), g.work, b->bst, b->stream));
+            BCK(b, cudaEventRecord(ev.e0, b->stream));
+            BCK(b, launch_test_batch((int)b->mode, g.awp, shape_cpw(k), g.d_inst[k], (uint32_t)g.members.size(),
+                                     g.n_tiles[k], g.work, gr, b->bst, gd, b->stream));
+            BCK(b, cudaEventRecord(ev.e1, b->stream));
+            BCK(b, cudaEventSynchronize(ev.e1));
+            float ms = 0.f;
+            BCK(b, cudaEventElapsedTime(&ms, ev.e0, ev.e1));
+            if (ms < ms_min) ms_min = ms;
+          }
+          if (ms_min < best) {
+            best = ms_min;
+            best_grab = gr;
+            best_grid = gd;
+            best_shape = k;
+          }
         }
-        if (ms_min < best) {
-          best = ms_min;
-          best_grab = gr;
-          best_grid = gd;
-        }
-      }
+    }
+    g.shape = best_shape;
     g.grab = best_grab;
     g.grid = best_grid;
     total += best;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   b->tuned_us = total * 1e3f;
   b->tuned = true;
   if (cache_path && *cache_path) {  // append this batch's choices (a later line wins on reading)
     std::lock_guard<std::mutex> lk(g_cache_mutex);
     std::ofstream f(cache_path, std::ios::app);
-    for (const Group& g : b->groups) f << cache_key(b, g) << ' ' << g.grab << ' ' << g.grid << '\n';
+    for (const Group& g : b->groups)
+      f << cache_key(b, g) << ' ' << g.grab << ' ' << g.grid << ' ' << shape_cpw(g.shape) << '\n';
   }
   return GSS_OK;
 }
@@ -490,7 +521,8 @@ int gss_batch_get_info(const gss_batch* b, gss_batch_info* out) {
     if (k >= 3) break;
     out->tiles_per_steal[k] = g.grab;
     out->grid[k] = (uint32_t)g.grid;
-    out->n_tiles[k] = g.n_tiles;
+    out->clauses_per_tile[k] = (uint32_t)shape_cpw(g.shape);
+    out->n_tiles[k] = g.n_tiles[g.shape];
     ++k;
   }
   out->n_groups = k;

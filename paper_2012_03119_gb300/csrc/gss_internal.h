@@ -118,10 +118,12 @@ cudaError_t launch_build_heads(const uint64_t* boff, uint64_t n, uint64_t L0, ui
 
 // Test clauses [c_lo, c_hi) against the planes; append records.  With wm (device, n_wm
 // entries, non-decreasing), clause c is tested against plane word w only if c < wm[w].
+// cpw: tile shape, 32 clauses per warp tile (one lane each) or 16 (two lanes each: head0 and
+// head1 of a clause in parallel); the wide build always takes 32.
 cudaError_t launch_test(int mode, const ClauseView& db, uint64_t c_lo, uint64_t c_hi, const PlaneView& pv,
                         gss_report* rec, uint64_t cap, DevStatus* st, int grid, cudaStream_t s,
                         const uint64_t* wm = nullptr, uint32_t n_wm = 0, const ActivityView& av = ActivityView{},
-                        const WideView& wide = WideView{});
+                        const WideView& wide = WideView{}, int cpw = 32);
 
 // Group a serving launch's records by plane word (request) into out: records of word w at
 // [sum of count[0..w), + count[w]), their mask ANDed with nmask[w], records left without a bit
@@ -156,14 +158,16 @@ cudaError_t launch_compact_copy(const uint64_t* off, const uint32_t* lits, const
                                 cudaStream_t s);
 
 // Occupancy-derived persistent grid for launch_test on this device.
-int test_grid_size(int mode, uint32_t AWp, int n_sms, bool wide = false);
+int test_grid_size(int mode, uint32_t AWp, int n_sms, bool wide = false, int cpw = 32);
+// Default tile shape for a database of m clauses and L literals (see k_test.cu).
+int test_tile_shape(uint64_t m, uint64_t L);
 
 // One instance of a batch as the batched test kernel sees it.
 struct BatchInst {
   ClauseView db;
   PlaneView pv;
   uint64_t m;      // clauses
-  uint64_t tile0;  // index of the instance's first 32-clause tile among all the batch's tiles
+  uint64_t tile0;  // index of the instance's first tile among all the batch's tiles (of the launch's shape)
   gss_report* rec;
   uint64_t cap;
   DevStatus* st;   // the instance's test status (records, bad codes)
@@ -174,8 +178,9 @@ cudaError_t launch_batch_reset(const BatchInst* d_inst, uint32_t n_inst, unsigne
                                cudaStream_t s);
 // Test every instance (all with the same AWp) in one persistent launch; warps take `grab`
 // tiles at a time from the device counter *work (zeroed by launch_batch_reset).
-cudaError_t launch_test_batch(int mode, uint32_t AWp, const BatchInst* d_inst, uint32_t n_inst, uint64_t n_tiles,
-                              unsigned long long* work, uint32_t grab, DevStatus* bst, int grid, cudaStream_t s);
-int test_batch_grid_size(int mode, uint32_t AWp, int n_sms);
+cudaError_t launch_test_batch(int mode, uint32_t AWp, int cpw, const BatchInst* d_inst, uint32_t n_inst,
+                              uint64_t n_tiles, unsigned long long* work, uint32_t grab, DevStatus* bst, int grid,
+                              cudaStream_t s);
+int test_batch_grid_size(int mode, uint32_t AWp, int cpw, int n_sms);
 
 }  // namespace gss

@@ -171,7 +171,9 @@ extern "C" int gss_test_noalloc(const uint64_t* d_offsets, uint64_t n_clauses, c
   cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev);
   const ClauseView db{off, d_lits, head0, head1, 2u * n_vars};
   const PlaneView pv{P, aggF, aggU, Wp, AWp, n_assign, n_vars};
-  NA_CK(launch_test((int)mode, db, 0, n_clauses, pv, d_out, cap, st, test_grid_size((int)mode, AWp, n_sms), s));
+  const int cpw = test_tile_shape(n_clauses, L);
+  NA_CK(launch_test((int)mode, db, 0, n_clauses, pv, d_out, cap, st, test_grid_size((int)mode, AWp, n_sms, false, cpw), s,
+                    nullptr, 0, ActivityView{}, WideView{}, cpw));
   NA_CK(cudaMemcpyAsync(d_count, &st->n_records, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
   NA_CK(cudaMemcpyAsync(h, st, sizeof h, cudaMemcpyDeviceToHost, s));
   NA_CK(cudaStreamSynchronize(s));

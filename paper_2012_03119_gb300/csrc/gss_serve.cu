@@ -55,7 +55,8 @@ constexpr uint32_t MAX_LANES = 8;
 
 struct Request {
   uint32_t slot = 0, n = 0;
-  uint64_t wm = 0;
+  uint64_t wm = 0;      // watermark: clause ids below it
+  uint64_t wm_pos = 0;  // the same bound in positions of the database the launch read
   bool keep = false, done = false, overflow = false, bad = false;
   uint32_t waiters = 0;  // clients inside gss_server_wait on it: never dropped meanwhile
   uint32_t batch_words = 0;
@@ -115,7 +116,18 @@ struct gss_server {
   std::deque<uint64_t> ready;
   std::unordered_map<uint64_t, Request> reqs;
   uint64_t next_id = 1;
-  std::atomic<uint64_t> committed{0};
+  std::atomic<uint64_t> committed{0};  // clause ids below this are committed (visible to new requests)
+  std::atomic<uint64_t> resident{0};   // clauses held (fewer than committed once a reduction removed some)
+  uint64_t max_clauses = 0, max_lits = 0;
+  // clause activity (Section 3.6): each launch is one test for the bumps; off until enabled
+  bool activity = false;
+  float act_inc = 1.0f, act_inv_decay = 1.0f;
+  uint32_t act_epoch = 0;
+  // after a reduction, the ids of the resident clauses in position order (host copy), to turn
+  // a request's watermark (a clause id bound) into a position bound at launch time
+  bool reduced = false, reducing = false;
+  std::vector<uint32_t> h_ids;
+  uint64_t reductions = 0, removed = 0;
   std::thread sched;
   bool stop = false, closed = false;  // closed: the scheduler has exited
   int sched_err = GSS_OK;
@@ -169,6 +181,13 @@ void CUDART_CB lane_done(void* p) {
   wake_scheduler(L->srv);
 }
 
+// Position bound of a watermark (a clause id bound): the number of resident clauses whose
+// id is below it (v->mu held).  Ids grow with position, so this is a lower bound search.
+uint64_t position_bound(const gss_server* v, uint64_t wm) {
+  if (!v->reduced) return wm;  // ids are positions until the first reduction
+  return (uint64_t)(std::lower_bound(v->h_ids.begin(), v->h_ids.end(), wm) - v->h_ids.begin());
+}
+
 // Start a launch on lane L with the oldest admitted requests (v->mu held).
 cudaError_t start_launch(gss_server* v, Lane& L) {
   TraceRange tr("gss_server launch");
@@ -183,9 +202,9 @@ cudaError_t start_launch(gss_server* v, Lane& L) {
     r.batch_words = k;
     r.t_launch = Clock::now();
     L.h_in->rows[w] = r.slot * 32u;
-    L.h_in->wm[w] = r.wm;
+    L.h_in->wm[w] = r.wm_pos = position_bound(v, r.wm);  // clause positions < this have ids < the watermark
     L.h_in->nmask[w] = r.n >= 32 ? 0xFFFFFFFFu : ((1u << r.n) - 1u);
-    max_wm = std::max(max_wm, r.wm);
+    max_wm = std::max(max_wm, L.h_in->wm[w]);
   }
   const uint32_t N = 32u * k;
   const uint32_t Wp = words_stride(N), AWp = agg_stride(Wp);
@@ -207,7 +226,17 @@ cudaError_t start_launch(gss_server* v, Lane& L) {
     // mode a unit clause triggers on them), so they never count against the launch's capacity
     PlaneView pv{L.P, L.aggF, L.aggU, Wp, AWp, N, v->V};
     pv.wvalid = L.d_in->nmask;
-    e = launch_test((int)v->mode, v->db, 0, max_wm, pv, L.rec, L.cap, &L.d_out->st, v->grid, L.s, L.d_in->wm, k);
+    ActivityView av;
+    if (v->activity) av = ActivityView{v->ctx->act, v->ctx->stamp, v->act_epoch, v->act_inc};
+    e = launch_test((int)v->mode, v->db, 0, max_wm, pv, L.rec, L.cap, &L.d_out->st, v->grid, L.s, L.d_in->wm, k, av);
+  }
+  if (v->activity) {  // the launch was one test: the increment grows, rescaled past 1e20 after its bumps
+    v->act_epoch = v->act_epoch + 1 == 0xFFFFFFFFu ? 0 : v->act_epoch + 1;
+    v->act_inc = v->act_inc * v->act_inv_decay;
+    if (e == cudaSuccess && v->act_inc > 1e20f) {
+      e = launch_scale_f32(v->ctx->act, v->resident.load(), 1e-20f, L.s);  // before the next launch's test
+      v->act_inc = v->act_inc * 1e-20f;
+    }
   }
   if (e == cudaSuccess) e = cudaLaunchHostFunc(L.s, lane_tested, &L);
   if (e == cudaSuccess)
@@ -238,7 +267,7 @@ void finish_launch(gss_server* v, Lane& L) {
     q.bad = ((pst.bad_code >> w) & 1u) != 0u || st.timeout != 0u || pst.timeout != 0u;
     q.t_done = now;
     v->lat_us.push_back(std::chrono::duration<double, std::micro>(q.t_done - q.t_submit).count());
-    v->pair_tests += q.wm * (uint64_t)q.n;
+    v->pair_tests += q.wm_pos * (uint64_t)q.n;
     v->completed += 1;
     v->free_slots.push_back(q.slot);
     if (!q.keep) v->reqs.erase(L.ids[w]);
@@ -278,7 +307,7 @@ void scheduler(gss_server* v) {
     // a new launch takes every waiting request; it starts only while fewer than
     // tests_in_flight tests run, so that requests gather into larger launches under load
     for (Lane& L : v->lanes) {
-      if (v->stop || v->ready.empty() || L.busy || testing >= v->tests_in_flight) continue;
+      if (v->stop || v->reducing || v->ready.empty() || L.busy || testing >= v->tests_in_flight) continue;
       ++testing;
       const cudaError_t e = start_launch(v, L);
       if (e != cudaSuccess && v->sched_err == GSS_OK) {
@@ -409,6 +438,8 @@ int gss_server_create(gss_server** out, uint32_t n_vars, const gss_server_config
     return rc;
   }
   rc = reserve_db(v->ctx, cfg.max_clauses, cfg.max_lits);
+  v->max_clauses = cfg.max_clauses;
+  v->max_lits = cfg.max_lits;
   bool ok = rc == GSS_OK && cudaSetDevice(cfg.device) == cudaSuccess;
   if (ok) v->db = ClauseView{v->ctx->off, v->ctx->lits, v->ctx->head0, v->ctx->head1, 2u * n_vars};
   ok = ok && cudaStreamCreateWithFlags(&v->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
@@ -467,16 +498,135 @@ int gss_server_add_clauses(gss_server* v, const uint64_t* offsets, uint64_t n, c
   gss_ctx* c = v->ctx;
   if (n && !offsets) return sfail(v, GSS_E_INVAL, "offsets is NULL");
   const uint64_t L = n ? offsets[n] : 0;
-  if (c->m + n + 1 > c->cap_m || (c->m + n) * 8 > c->cap_head0 || c->L + L > c->cap_L)
+  if (c->m + n + 1 > c->cap_m || (c->m + n) * 8 > c->cap_head0 || c->L + L > c->cap_L ||
+      (c->act && c->m + n > c->cap_act) || (c->ext && c->m + n > c->cap_ext))
     return sfail(v, GSS_E_NOMEM, "reserved database capacity exceeded (%llu clauses, %llu literals reserved)",
                  (unsigned long long)(c->cap_m - 1), (unsigned long long)c->cap_L);
-  int rc = gss_add_clauses(c, offsets, n, lits, first_id);
+  {
+    std::lock_guard<std::mutex> g(v->mu);
+    c->inc = v->act_inc;  // a new clause starts at the current increment
+  }
+  uint32_t first = 0;
+  int rc = gss_add_clauses(c, offsets, n, lits, &first);
   if (rc) return sfail(v, rc, "%s", gss_last_error(c));
+  if (first_id) *first_id = first;
   cudaError_t e = cudaStreamSynchronize(c->stream);  // rows complete before any request may see them
   if (e != cudaSuccess) return sfail(v, GSS_E_CUDA, "ingest: %s", cudaGetErrorString(e));
   v->map.store(c->map);
-  v->committed.store(c->m);
+  if (v->reduced) {
+    std::lock_guard<std::mutex> g(v->mu);
+    for (uint64_t i = 0; i < n; ++i) v->h_ids.push_back(first + (uint32_t)i);
+  }
+  v->resident.store(c->m);
+  v->committed.store(c->next_id);
   return GSS_OK;
+}
+
+// Wait until no launch runs and none starts (ingest_mu held): the database may then change.
+static int drain_launches(gss_server* v) {
+  std::unique_lock<std::mutex> lk(v->mu);
+  v->reducing = true;
+  v->cv_done.wait(lk, [&] {
+    bool busy = false;
+    for (const Lane& L : v->lanes) busy |= L.busy;
+    return !busy || v->sched_err != GSS_OK || v->closed;
+  });
+  if (v->sched_err != GSS_OK) {
+    v->reducing = false;
+    return sfail(v, v->sched_err, "scheduler stopped: %s", v->sched_msg.c_str());
+  }
+  return GSS_OK;
+}
+
+static void resume_launches(gss_server* v) {
+  {
+    std::lock_guard<std::mutex> g(v->mu);
+    v->reducing = false;
+  }
+  wake_scheduler(v);
+}
+
+int gss_server_set_activity(gss_server* v, float decay) {
+  if (!v) return GSS_E_INVAL;
+  if (!(decay > 0.0f && decay <= 1.0f)) return sfail(v, GSS_E_INVAL, "decay must be in (0, 1]");
+  if (v->tests_in_flight != 1)
+    return sfail(v, GSS_E_STATE, "activity needs tests_in_flight = 1 (one test bumps at a time)");
+  std::lock_guard<std::mutex> g(v->ingest_mu);
+  int rc = drain_launches(v);
+  if (rc) return rc;
+  gss_ctx* c = v->ctx;
+  const bool first = c->act == nullptr;
+  rc = gss_set_activity(c, decay);
+  if (!rc) rc = reserve_clause_arrays(c, v->max_clauses);  // the arrays never move under a launch
+  if (rc) {
+    resume_launches(v);
+    return sfail(v, rc, "%s", gss_last_error(c));
+  }
+  {
+    std::lock_guard<std::mutex> lk(v->mu);
+    if (first) {
+      v->act_inc = 1.0f;
+      v->act_epoch = 0;
+    }
+    v->act_inv_decay = c->inv_decay;
+    v->activity = true;
+  }
+  resume_launches(v);
+  return GSS_OK;
+}
+
+int gss_server_reduce(gss_server* v, double remove_fraction, uint64_t* n_removed) {
+  if (!v) return GSS_E_INVAL;
+  if (n_removed) *n_removed = 0;
+  TraceRange tr("gss_server_reduce");
+  std::lock_guard<std::mutex> g(v->ingest_mu);
+  if (!v->activity) return sfail(v, GSS_E_STATE, "gss_server_reduce needs activities (gss_server_set_activity)");
+  int rc = drain_launches(v);
+  if (rc) return rc;
+  gss_ctx* c = v->ctx;
+  uint64_t n = 0;
+  rc = gss_reduce_db(c, remove_fraction, &n);
+  // the compacted arrays are sized to the kept clauses: reserve them again, so that later
+  // ingest never moves them under a running launch
+  if (!rc) rc = reserve_db(c, v->max_clauses, v->max_lits);
+  if (!rc) rc = reserve_clause_arrays(c, v->max_clauses);
+  std::vector<uint32_t> ids(c->m);
+  if (!rc && c->m) {
+    const cudaError_t e = c->ext ? cudaMemcpy(ids.data(), c->ext, c->m * sizeof(uint32_t), cudaMemcpyDeviceToHost)
+                                 : cudaErrorInvalidValue;
+    if (e != cudaSuccess) rc = fail(c, GSS_E_CUDA, "clause ids: %s", cudaGetErrorString(e));
+  }
+  if (rc) {  // gss_reduce_db leaves the database unchanged on failure; a failed reservation leaves it valid
+    resume_launches(v);
+    return sfail(v, rc, "%s", gss_last_error(c));
+  }
+  {
+    std::lock_guard<std::mutex> lk(v->mu);
+    v->db = ClauseView{c->off, c->lits, c->head0, c->head1, 2u * c->V, c->ext};
+    v->h_ids.swap(ids);
+    v->reduced = true;
+    v->reductions += 1;
+    v->removed += n;
+  }
+  v->resident.store(c->m);
+  resume_launches(v);
+  if (n_removed) *n_removed = n;
+  return GSS_OK;
+}
+
+// Copies of the server context's per-clause arrays (activities, ids), in position order.
+int gss_server_get_activity(gss_server* v, float* out, uint64_t cap, uint64_t* n_out) {
+  if (!v) return GSS_E_INVAL;
+  std::lock_guard<std::mutex> g(v->ingest_mu);
+  const int rc = gss_get_activity(v->ctx, out, cap, n_out);
+  return rc ? sfail(v, rc, "%s", gss_last_error(v->ctx)) : GSS_OK;
+}
+
+int gss_server_get_clause_ids(gss_server* v, uint32_t* out, uint64_t cap, uint64_t* n_out) {
+  if (!v) return GSS_E_INVAL;
+  std::lock_guard<std::mutex> g(v->ingest_mu);
+  const int rc = gss_get_clause_ids(v->ctx, out, cap, n_out);
+  return rc ? sfail(v, rc, "%s", gss_last_error(v->ctx)) : GSS_OK;
 }
 
 int gss_server_submit(gss_server* v, const uint8_t* values, uint32_t n_assign, uint64_t watermark, int64_t wait_us,
@@ -580,7 +730,10 @@ int gss_server_get_stats(gss_server* v, gss_server_stats* o) {
     o->words_launched = v->words;
     o->pair_tests = v->pair_tests;
     o->reports = v->reports;
-    o->committed_clauses = v->committed.load();
+    o->committed_clauses = v->resident.load();
+    o->next_clause_id = v->committed.load();
+    o->reductions = v->reductions;
+    o->clauses_removed = v->removed;
     o->expired = v->expired;
     o->slots = v->n_slots;
     l = v->lat_us;

@@ -177,14 +177,23 @@ __device__ __forceinline__ void load8_csr(const uint32_t* __restrict__ lits, uin
   for (int j = 0; j < 8; ++j) l[j] = (k0 + j < e) ? __ldg(lits + k0 + j) : pad;
 }
 
+__device__ __forceinline__ void load8_smem(const uint32_t* p, uint32_t (&l)[8]) {
+  const uint4 a = reinterpret_cast<const uint4*>(p)[0], b = reinterpret_cast<const uint4*>(p)[1];
+  l[0] = a.x; l[1] = a.y; l[2] = a.z; l[3] = a.w;
+  l[4] = b.x; l[5] = b.y; l[6] = b.z; l[7] = b.w;
+}
+
 // The exact recurrence of a (clause, word) pair past its first 8 literals (head0, already
-// applied): literals 8..15 from head1, then the CSR, while the word is alive.
+// applied): literals 8..15 from head1 (h1s: the clause's head1 in shared memory, or nullptr
+// to read it from global memory), then the CSR, while the word is alive.
 template <int MODE>
-__device__ __forceinline__ void exact_tail(const ClauseView& db, const PlaneView& pv, uint64_t c, uint32_t g,
-                                           uint32_t valid, uint32_t last_head0, uint32_t& af, uint32_t& ou) {
+__device__ __forceinline__ void exact_tail(const ClauseView& db, const PlaneView& pv, uint64_t c, const uint32_t* h1s,
+                                           uint32_t g, uint32_t valid, uint32_t last_head0, uint32_t& af,
+                                           uint32_t& ou) {
   uint32_t l[8];
   if ((af | ou) != 0u && last_head0 != db.pad) {
-    load8_global(db.head1 + c * 8u, l);
+    if (h1s) load8_smem(h1s, l);
+    else load8_global(db.head1 + c * 8u, l);
     word_batch8<MODE>(pv, l, g, valid, af, ou);
     if ((af | ou) != 0u && l[7] != db.pad) {
       const uint64_t e = db.off[c + 1];
@@ -314,12 +323,13 @@ __device__ __forceinline__ void out_append(Smem& S, Outbox& o, bool has, uint32_
   o.n += k;
 }
 
-// Stage B proper: the exact recurrence of np staged pairs buf[0 .. np) (owner lane | group << 5,
-// the owner's head0 in ring), one pair per lane, records into the outbox.
+// Stage B proper: the exact recurrence of np staged pairs buf[0 .. np) (owner | group << 5, the
+// owner being the clause's index in the tile, its head0 at ring + 8 owner and, when ring1 is
+// not null, its head1 at ring1 + 8 owner), one pair per lane, records into the outbox.
 template <int MODE, bool EXTRA, typename Smem>
 __device__ __forceinline__ void exact_pairs(const ClauseView& db, const PlaneView& pv, Smem& S, const uint32_t* ring,
-                                            const uint32_t* buf, uint32_t np, uint64_t c0, uint32_t lane, Outbox& out,
-                                            const ActivityView& av) {
+                                            const uint32_t* ring1, const uint32_t* buf, uint32_t np, uint64_t c0,
+                                            uint32_t lane, Outbox& out, const ActivityView& av) {
   for (uint32_t p0 = 0; p0 < np; p0 += 32u) {
     const uint32_t pa = p0 + lane;
     const bool ha = pa < np;
@@ -330,7 +340,7 @@ __device__ __forceinline__ void exact_pairs(const ClauseView& db, const PlaneVie
     const uint32_t va = valid_bits(pv.N, ga) & ((pv.wvalid && ha) ? __ldg(pv.wvalid + ga) : FULL);  // real rows only
     uint32_t afa = ha ? ((MODE == GSS_MODE_ALLF) ? FULL : va) : 0u, oua = 0u;
     word_batch8<MODE>(pv, la, ga, va, afa, oua);
-    exact_tail<MODE>(db, pv, c0 + oa, ga, va, la[7], afa, oua);
+    exact_tail<MODE>(db, pv, c0 + oa, ring1 ? ring1 + oa * 8u : nullptr, ga, va, la[7], afa, oua);
     const uint32_t ra = afa | oua;
     const uint64_t cp = c0 + oa;  // position of the pair's clause
     uint32_t id = (uint32_t)cp;
@@ -381,40 +391,118 @@ __device__ __forceinline__ void live_words(const uint64_t* wm, uint32_t n_wm, ui
 // apart from positions and/or activities to bump (a separate build of the kernel, so that
 // databases without them pay nothing).  WIDE (with AW == 1): pv's aggregate rows are the
 // level-2 rows and stage A's bits are super-groups; wv holds the level-1 rows.
-template <int MODE, int AW, bool EXTRA = false, bool WIDE = false, typename Smem>
+// Stage A with two lanes per clause (16 clauses per tile): lane 2i + h starts on head h of
+// clause i.  Each lane runs the recurrence over its own 8 literals, the even lane from the
+// clause's live words, the odd one from the identity (all ones, nothing U-implied); the two
+// segment results compose -- the recurrence is linear over the bits, so (A0, O0) then
+// (A1, O1) give (A0 A1, O0 A1 | A0 O1) -- and both lanes continue with the composed state
+// over 16 CSR literals per round, 8 each.  mask: the two lanes of the pair.
+template <int MODE, int AW>
+__device__ __forceinline__ void compose_pair(uint32_t (&af)[AW], uint32_t (&ou)[AW], uint32_t half, uint32_t mask) {
+#pragma unroll
+  for (int i = 0; i < AW; ++i) {
+    const uint32_t pa = __shfl_xor_sync(mask, af[i], 1), po = __shfl_xor_sync(mask, ou[i], 1);
+    if constexpr (MODE == GSS_MODE_ALLF) {
+      af[i] &= pa;
+    } else {
+      const uint32_t a0 = half ? pa : af[i], o0 = half ? po : ou[i];  // even lane's segment first
+      const uint32_t a1 = half ? af[i] : pa, o1 = half ? ou[i] : po;
+      af[i] = a0 & a1;
+      ou[i] = (o0 & a1) | (a0 & o1);
+    }
+  }
+}
+
+template <int MODE, int AW>
+__device__ __forceinline__ void stage_a_paired(const ClauseView& db, const PlaneView& pv, const uint32_t* ring,
+                                               uint64_t c0, uint64_t c_hi, uint32_t lane, const uint64_t* wm,
+                                               uint32_t n_wm, uint32_t (&af)[AW], uint32_t (&ou)[AW]) {
+  const uint32_t PAD = db.pad;
+  const uint32_t ci = lane >> 1, half = lane & 1u;
+  const uint64_t c = c0 + ci;
+  const bool act = c < c_hi;
+  live_words<AW>(wm, n_wm, c, af);
+#pragma unroll
+  for (int i = 0; i < AW; ++i) { af[i] = act ? (half ? FULL : af[i]) : 0u; ou[i] = 0u; }
+  uint32_t l[8];
+  if (act) load8_smem(ring + half * 128u + ci * 8u, l);
+  else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) l[j] = PAD;
+  }
+  // more than 16 literals: the odd lane's head1 is full; the rest is in the CSR
+  const bool tail = __shfl_sync(FULL, l[7], lane | 1u) != PAD && act;
+  uint64_t b = 0, e = 0;
+  if (tail) {  // in flight during the head batch
+    b = __ldg(db.off + c);
+    e = __ldg(db.off + c + 1);
+  }
+  if (act) group_batch8<MODE, AW>(pv, l, af, ou);
+  compose_pair<MODE, AW>(af, ou, half, FULL);
+  if (tail && any2<AW>(af, ou)) {
+    const uint32_t mask = 3u << (lane & ~1u);  // both lanes of the pair take the same iterations
+    for (uint64_t k0 = b + HEAD_K; k0 < e && any2<AW>(af, ou); k0 += 16) {
+      load8_csr(db.lits, k0 + 8u * half, e, PAD, l);
+      if (half) {  // the odd lane's chunk starts from the identity
+#pragma unroll
+        for (int i = 0; i < AW; ++i) { af[i] = FULL; ou[i] = 0u; }
+      }
+      group_batch8<MODE, AW>(pv, l, af, ou);
+      compose_pair<MODE, AW>(af, ou, half, mask);
+    }
+  }
+}
+
+// Stage A and stage B for the tile of clauses [c0, min(c0 + CPW, c_hi)), whose heads are in
+// S.ring[s] (CPW = 32: head0 of each lane's clause; CPW = 16: head0 of the 16 clauses, then
+// their head1); records are staged in the warp's outbox.  EXTRA: the database has clause ids
+// apart from positions and/or activities to bump (a separate build of the kernel, so that
+// databases without them pay nothing).  WIDE (with AW == 1, CPW == 32): pv's aggregate rows
+// are the level-2 rows and stage A's bits are super-groups; wv holds the level-1 rows.
+template <int MODE, int AW, bool EXTRA = false, bool WIDE = false, int CPW = 32, typename Smem>
 __device__ __forceinline__ void test_tile(const ClauseView& db, const PlaneView& pv, Smem& S,
                                           int s, uint64_t c0, uint64_t c_hi, uint32_t lane, Outbox& out,
                                           const uint64_t* wm = nullptr, uint32_t n_wm = 0,
                                           const ActivityView& av = ActivityView{}, const WideView& wv = WideView{}) {
   static_assert(!WIDE || AW == 1, "wide sets have one level-2 word per row");
+  static_assert(CPW == 32 || (CPW == 16 && !WIDE), "tile shapes: 32 clauses, or 16 with two lanes each");
   const uint32_t PAD = db.pad;
+  uint32_t af[AW], ou[AW];
+  if constexpr (CPW == 16) {
+    // ---------------- stage A: group test, two lanes per clause
+    stage_a_paired<MODE, AW>(db, pv, S.ring[s], c0, c_hi, lane, wm, n_wm, af, ou);
+    if (lane & 1u) {  // the even lane of a pair owns its candidates
+#pragma unroll
+      for (int i = 0; i < AW; ++i) { af[i] = 0u; ou[i] = 0u; }
+    }
+  } else {
   const uint64_t c = c0 + lane;
   const bool act = c < c_hi;
   const uint32_t* h0 = &S.ring[s][lane * 8u];
 
   // ---------------- stage A: group (aggregate) test of this lane's clause
-  uint32_t af[AW], ou[AW];
   live_words<AW>(wm, n_wm, c, af);
 #pragma unroll
   for (int i = 0; i < AW; ++i) { af[i] = act ? af[i] : 0u; ou[i] = 0u; }
   if (act) {
     uint32_t l[8], l1[8];
-    const uint4 a = reinterpret_cast<const uint4*>(h0)[0], b = reinterpret_cast<const uint4*>(h0)[1];
-    l[0] = a.x; l[1] = a.y; l[2] = a.z; l[3] = a.w;
-    l[4] = b.x; l[5] = b.y; l[6] = b.z; l[7] = b.w;
+    load8_smem(h0, l);
     const bool long_clause = l[7] != PAD;
     if (long_clause) load8_global(db.head1 + c * 8u, l1);  // in flight during the first batch
     group_batch8<MODE, AW>(pv, l, af, ou);
     if (long_clause && any2<AW>(af, ou)) {
+      const bool tail = l1[7] != PAD;
+      uint64_t b = 0, e = 0;
+      if (tail) { b = __ldg(db.off + c); e = __ldg(db.off + c + 1); }  // in flight during the second batch
       group_batch8<MODE, AW>(pv, l1, af, ou);
-      if (l1[7] != PAD && any2<AW>(af, ou)) {
-        const uint64_t e = db.off[c + 1];
-        for (uint64_t k0 = db.off[c] + HEAD_K; k0 < e && any2<AW>(af, ou); k0 += 8) {
+      if (tail && any2<AW>(af, ou)) {
+        for (uint64_t k0 = b + HEAD_K; k0 < e && any2<AW>(af, ou); k0 += 8) {
           load8_csr(db.lits, k0, e, PAD, l);
           group_batch8<MODE, AW>(pv, l, af, ou);
         }
       }
     }
+  }
   }
   uint32_t cand[AW];
 #pragma unroll
@@ -438,7 +526,7 @@ __device__ __forceinline__ void test_tile(const ClauseView& db, const PlaneView&
       while (cand[i] != 0u && pos < PAIR_CAP) {
         const uint32_t bit = (uint32_t)(__ffs(cand[i]) - 1);
         cand[i] &= cand[i] - 1u;
-        S.pairs[pos++] = lane | ((32u * i + bit) << 5);
+        S.pairs[pos++] = (CPW == 16 ? lane >> 1 : lane) | ((32u * i + bit) << 5);
       }
     }
     __syncwarp();
@@ -467,18 +555,30 @@ __device__ __forceinline__ void test_tile(const ClauseView& db, const PlaneView&
             S.pairs2[q++] = oa | ((32u * sg + b) << 5);
           }
           __syncwarp();
-          exact_pairs<MODE, EXTRA>(db, pv, S, S.ring[s], S.pairs2, t1 < PAIR_CAP ? t1 : PAIR_CAP, c0, lane, out, av);
+          exact_pairs<MODE, EXTRA>(db, pv, S, S.ring[s], nullptr, S.pairs2, t1 < PAIR_CAP ? t1 : PAIR_CAP, c0, lane,
+                                   out, av);
           __syncwarp();
         }
       }
     } else {
-      exact_pairs<MODE, EXTRA>(db, pv, S, S.ring[s], S.pairs, np, c0, lane, out, av);
+      exact_pairs<MODE, EXTRA>(db, pv, S, S.ring[s], CPW == 16 ? &S.ring[s][128] : nullptr, S.pairs, np, c0, lane,
+                               out, av);
     }
     __syncwarp();
   }
 }
 
-template <int MODE, int AW, bool EXTRA, bool WIDE = false>
+// Lane 0: bulk-copy the heads of the n clauses from c0 into ring stage `stage`: head0 (CPW =
+// 32), or head0 then head1 of the 16 clauses of a paired-lane tile (CPW = 16).
+template <int CPW, typename Smem>
+__device__ __forceinline__ void issue_heads(Smem& S, int stage, const ClauseView& db, uint64_t c0, uint32_t n) {
+  ptx::fence_proxy_async();
+  ptx::mbar_expect_tx(&S.bar[stage], (CPW == 16 ? 2u : 1u) * n * 32u);
+  ptx::bulk_g2s(S.ring[stage], db.head0 + c0 * 8u, n * 32u, &S.bar[stage]);
+  if constexpr (CPW == 16) ptx::bulk_g2s(&S.ring[stage][128], db.head1 + c0 * 8u, n * 32u, &S.bar[stage]);
+}
+
+template <int MODE, int AW, bool EXTRA, bool WIDE = false, int CPW = 32>
 __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c_lo, uint64_t c_hi, PlaneView pv,
                                                        gss_report* __restrict__ rec, uint64_t cap, DevStatus* st,
                                                        const uint64_t* __restrict__ wm, uint32_t n_wm,
@@ -495,7 +595,7 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c
   Smem& S = smem[wib];
   const uint64_t warp_id = (uint64_t)blockIdx.x * TEST_WARPS + wib;
   const uint64_t n_warps = (uint64_t)gridDim.x * TEST_WARPS;
-  const uint64_t n_tiles = (c_hi - c_lo + 31) / 32;
+  const uint64_t n_tiles = (c_hi - c_lo + CPW - 1) / CPW;
   if (warp_id >= n_tiles) return;
 
   if (lane == 0) {
@@ -504,13 +604,10 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c
     ptx::fence_mbar_init();
   }
   __syncwarp();
-  auto issue = [&](uint64_t tile, int stage) {  // lane 0: bulk-copy the tile's head0 into ring[stage]
-    const uint64_t c0 = c_lo + tile * 32u;
+  auto issue = [&](uint64_t tile, int stage) {  // lane 0: bulk-copy the tile's heads into ring[stage]
+    const uint64_t c0 = c_lo + tile * CPW;
     const uint64_t left = c_hi - c0;
-    const uint32_t n = left < 32u ? (uint32_t)left : 32u;
-    ptx::fence_proxy_async();
-    ptx::mbar_expect_tx(&S.bar[stage], n * 32u);
-    ptx::bulk_g2s(S.ring[stage], db.head0 + c0 * 8u, n * 32u, &S.bar[stage]);
+    issue_heads<CPW>(S, stage, db, c0, left < (uint64_t)CPW ? (uint32_t)left : (uint32_t)CPW);
   };
   if (lane == 0) issue(warp_id, 0);
 
@@ -530,7 +627,7 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test(ClauseView db, uint64_t c
       out_close(S, out, lane);
       return;
     }
-    test_tile<MODE, AW, EXTRA, WIDE>(db, pv, S, s, c_lo + t * 32u, c_hi, lane, out, wms, n_wm, av, wv);
+    test_tile<MODE, AW, EXTRA, WIDE, CPW>(db, pv, S, s, c_lo + t * CPW, c_hi, lane, out, wms, n_wm, av, wv);
     __syncwarp();
   }
   out_close(S, out, lane);
@@ -552,7 +649,7 @@ __device__ __forceinline__ uint32_t find_inst(const BatchInst* __restrict__ inst
 // `grab` consecutive tiles at a time from a device counter (work stealing), so instances of
 // very different sizes share the GPU without a launch each; the head0 copy of a warp's next
 // tile is in flight while the current one is tested, as in k_test.
-template <int MODE, int AW>
+template <int MODE, int AW, int CPW = 32>
 __global__ void __launch_bounds__(TEST_THREADS) k_test_batch(const BatchInst* __restrict__ inst, uint32_t n_inst,
                                                              uint64_t n_tiles, unsigned long long* __restrict__ work,
                                                              uint32_t grab, DevStatus* bst) {
@@ -570,14 +667,11 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test_batch(const BatchInst* __
     ptx::fence_mbar_init();
   }
   __syncwarp();
-  auto issue = [&](uint64_t t, int stage) {  // lane 0: bulk-copy tile t's head0 into ring[stage]
+  auto issue = [&](uint64_t t, int stage) {  // lane 0: bulk-copy tile t's heads into ring[stage]
     const BatchInst& d = inst[find_inst(inst, n_inst, t)];
-    const uint64_t c0 = (t - d.tile0) * 32u;
+    const uint64_t c0 = (t - d.tile0) * CPW;
     const uint64_t left = d.m - c0;
-    const uint32_t n = left < 32u ? (uint32_t)left : 32u;
-    ptx::fence_proxy_async();
-    ptx::mbar_expect_tx(&S.bar[stage], n * 32u);
-    ptx::bulk_g2s(S.ring[stage], d.db.head0 + c0 * 8u, n * 32u, &S.bar[stage]);
+    issue_heads<CPW>(S, stage, d.db, c0, left < (uint64_t)CPW ? (uint32_t)left : (uint32_t)CPW);
   };
   uint64_t t = cb;
   if (lane == 0) issue(t, 0);
@@ -614,7 +708,7 @@ __global__ void __launch_bounds__(TEST_THREADS) k_test_batch(const BatchInst* __
       cur = i;
     }
     if (!st->bad_code)
-      test_tile<MODE, AW>(db, pv, S, s, (t - inst[i].tile0) * 32u, inst[i].m, lane, out);
+      test_tile<MODE, AW, false, false, CPW>(db, pv, S, s, (t - inst[i].tile0) * CPW, inst[i].m, lane, out);
     __syncwarp();  // every lane is done with ring[s] before it is refilled
     if (!has_next) break;
     t = tn;
@@ -634,20 +728,29 @@ __global__ void k_batch_reset(const BatchInst* __restrict__ inst, uint32_t n_ins
   if (i < n_inst) *inst[i].st = DevStatus{};
 }
 
-template <int MODE, int AW, bool WIDE = false>
+template <int MODE, int AW, bool WIDE = false, int CPW = 32>
 void launch_one(const ClauseView& db, uint64_t c_lo, uint64_t c_hi, const PlaneView& pv, gss_report* rec,
                 uint64_t cap, DevStatus* st, int grid, cudaStream_t s, const uint64_t* wm, uint32_t n_wm,
                 const ActivityView& av, const WideView& wv) {
   if (db.ext || av.act)
-    k_test<MODE, AW, true, WIDE><<<grid, TEST_THREADS, 0, s>>>(db, c_lo, c_hi, pv, rec, cap, st, wm, n_wm, av, wv);
+    k_test<MODE, AW, true, WIDE, CPW><<<grid, TEST_THREADS, 0, s>>>(db, c_lo, c_hi, pv, rec, cap, st, wm, n_wm, av, wv);
   else
-    k_test<MODE, AW, false, WIDE><<<grid, TEST_THREADS, 0, s>>>(db, c_lo, c_hi, pv, rec, cap, st, wm, n_wm, av, wv);
+    k_test<MODE, AW, false, WIDE, CPW><<<grid, TEST_THREADS, 0, s>>>(db, c_lo, c_hi, pv, rec, cap, st, wm, n_wm, av,
+                                                                     wv);
 }
 
-template <int MODE, int AW, bool WIDE = false>
+template <int MODE, int AW>
+void launch_cpw(int cpw, const ClauseView& db, uint64_t c_lo, uint64_t c_hi, const PlaneView& pv, gss_report* rec,
+                uint64_t cap, DevStatus* st, int grid, cudaStream_t s, const uint64_t* wm, uint32_t n_wm,
+                const ActivityView& av, const WideView& wv) {
+  if (cpw == 16) launch_one<MODE, AW, false, 16>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av, wv);
+  else launch_one<MODE, AW, false, 32>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av, wv);
+}
+
+template <int MODE, int AW, bool WIDE = false, int CPW = 32>
 int grid_for(int n_sms) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_test<MODE, AW, false, WIDE>, TEST_THREADS, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_test<MODE, AW, false, WIDE, CPW>, TEST_THREADS, 0) !=
           cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
@@ -674,10 +777,11 @@ __global__ void k_agg2(const uint32_t* __restrict__ aggF1, const uint32_t* __res
   }
 }
 
-template <int MODE, int AW>
+template <int MODE, int AW, int CPW>
 int batch_grid_for(int n_sms) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_test_batch<MODE, AW>, TEST_THREADS, 0) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_test_batch<MODE, AW, CPW>, TEST_THREADS, 0) !=
+          cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
   return per_sm * n_sms;
@@ -691,12 +795,17 @@ cudaError_t launch_batch_reset(const BatchInst* d_inst, uint32_t n_inst, unsigne
   return cudaGetLastError();
 }
 
-cudaError_t launch_test_batch(int mode, uint32_t AWp, const BatchInst* d_inst, uint32_t n_inst, uint64_t n_tiles,
-                              unsigned long long* work, uint32_t grab, DevStatus* bst, int grid, cudaStream_t s) {
+cudaError_t launch_test_batch(int mode, uint32_t AWp, int cpw, const BatchInst* d_inst, uint32_t n_inst,
+                              uint64_t n_tiles, unsigned long long* work, uint32_t grab, DevStatus* bst, int grid,
+                              cudaStream_t s) {
   if (n_inst == 0 || n_tiles == 0) return cudaSuccess;
   if (grid < 1) grid = 1;
   if (grab < 1) grab = 1;
-#define GSS_BATCH_LAUNCH(M, A) k_test_batch<M, A><<<grid, TEST_THREADS, 0, s>>>(d_inst, n_inst, n_tiles, work, grab, bst)
+#define GSS_BATCH_LAUNCH(M, A)                                                                                   \
+  do {                                                                                                           \
+    if (cpw == 16) k_test_batch<M, A, 16><<<grid, TEST_THREADS, 0, s>>>(d_inst, n_inst, n_tiles, work, grab, bst); \
+    else k_test_batch<M, A, 32><<<grid, TEST_THREADS, 0, s>>>(d_inst, n_inst, n_tiles, work, grab, bst);          \
+  } while (0)
   if (mode == GSS_MODE_ALLF) {
     if (AWp == 1) GSS_BATCH_LAUNCH(GSS_MODE_ALLF, 1);
     else if (AWp == 2) GSS_BATCH_LAUNCH(GSS_MODE_ALLF, 2);
@@ -710,15 +819,17 @@ cudaError_t launch_test_batch(int mode, uint32_t AWp, const BatchInst* d_inst, u
   return cudaGetLastError();
 }
 
-int test_batch_grid_size(int mode, uint32_t AWp, int n_sms) {
+int test_batch_grid_size(int mode, uint32_t AWp, int cpw, int n_sms) {
+#define GSS_BGRID(M, A) (cpw == 16 ? batch_grid_for<M, A, 16>(n_sms) : batch_grid_for<M, A, 32>(n_sms))
   if (mode == GSS_MODE_ALLF) {
-    if (AWp == 1) return batch_grid_for<GSS_MODE_ALLF, 1>(n_sms);
-    if (AWp == 2) return batch_grid_for<GSS_MODE_ALLF, 2>(n_sms);
-    return batch_grid_for<GSS_MODE_ALLF, 4>(n_sms);
+    if (AWp == 1) return GSS_BGRID(GSS_MODE_ALLF, 1);
+    if (AWp == 2) return GSS_BGRID(GSS_MODE_ALLF, 2);
+    return GSS_BGRID(GSS_MODE_ALLF, 4);
   }
-  if (AWp == 1) return batch_grid_for<GSS_MODE_TRIGGER, 1>(n_sms);
-  if (AWp == 2) return batch_grid_for<GSS_MODE_TRIGGER, 2>(n_sms);
-  return batch_grid_for<GSS_MODE_TRIGGER, 4>(n_sms);
+  if (AWp == 1) return GSS_BGRID(GSS_MODE_TRIGGER, 1);
+  if (AWp == 2) return GSS_BGRID(GSS_MODE_TRIGGER, 2);
+  return GSS_BGRID(GSS_MODE_TRIGGER, 4);
+#undef GSS_BGRID
 }
 
 cudaError_t launch_agg2(const uint32_t* aggF1, const uint32_t* aggU1, uint32_t V, uint32_t AWp1, uint32_t* agg2F,
@@ -732,9 +843,11 @@ cudaError_t launch_agg2(const uint32_t* aggF1, const uint32_t* aggU1, uint32_t V
 
 cudaError_t launch_test(int mode, const ClauseView& db, uint64_t c_lo, uint64_t c_hi, const PlaneView& pv,
                         gss_report* rec, uint64_t cap, DevStatus* st, int grid, cudaStream_t s, const uint64_t* wm,
-                        uint32_t n_wm, const ActivityView& av, const WideView& wv) {
+                        uint32_t n_wm, const ActivityView& av, const WideView& wv, int cpw) {
   if (c_hi <= c_lo) return cudaSuccess;
-  const uint64_t tiles = (c_hi - c_lo + 31) / 32;
+  if (wv.aggF1) cpw = 32;  // the wide build has one tile shape
+  cpw = cpw == 16 ? 16 : 32;
+  const uint64_t tiles = (c_hi - c_lo + cpw - 1) / cpw;
   const uint64_t max_blocks = (tiles + TEST_WARPS - 1) / TEST_WARPS;
   if ((uint64_t)grid > max_blocks) grid = (int)max_blocks;
   if (grid < 1) grid = 1;
@@ -745,27 +858,39 @@ cudaError_t launch_test(int mode, const ClauseView& db, uint64_t c_lo, uint64_t 
     return cudaGetLastError();
   }
   if (mode == GSS_MODE_ALLF) {
-    if (pv.AWp == 1) launch_one<GSS_MODE_ALLF, 1>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av, wv);
-    else if (pv.AWp == 2) launch_one<GSS_MODE_ALLF, 2>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av, wv);
-    else launch_one<GSS_MODE_ALLF, 4>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av, wv);
+    if (pv.AWp == 1) launch_cpw<GSS_MODE_ALLF, 1>(cpw, db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av, wv);
+    else if (pv.AWp == 2) launch_cpw<GSS_MODE_ALLF, 2>(cpw, db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av, wv);
+    else launch_cpw<GSS_MODE_ALLF, 4>(cpw, db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av, wv);
   } else {
-    if (pv.AWp == 1) launch_one<GSS_MODE_TRIGGER, 1>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av, wv);
-    else if (pv.AWp == 2) launch_one<GSS_MODE_TRIGGER, 2>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av, wv);
-    else launch_one<GSS_MODE_TRIGGER, 4>(db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av, wv);
+    if (pv.AWp == 1) launch_cpw<GSS_MODE_TRIGGER, 1>(cpw, db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av, wv);
+    else if (pv.AWp == 2) launch_cpw<GSS_MODE_TRIGGER, 2>(cpw, db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av, wv);
+    else launch_cpw<GSS_MODE_TRIGGER, 4>(cpw, db, c_lo, c_hi, pv, rec, cap, st, grid, s, wm, n_wm, av, wv);
   }
   return cudaGetLastError();
 }
 
-int test_grid_size(int mode, uint32_t AWp, int n_sms, bool wide) {
+int test_tile_shape(uint64_t m, uint64_t L) {
+  // 32 clauses per tile.  Pairing lanes on long clauses halves a clause's chain of dependent
+  // gathers but also the clauses a warp has in flight; measured on GB300 it was slower on
+  // every workload, long clauses included (4M clauses of median 20 literals: 217 us against
+  // 168 us; 10M of median 40: 662 us against 445 us).  The batch autotuner still times both.
+  (void)m;
+  (void)L;
+  return 32;
+}
+
+int test_grid_size(int mode, uint32_t AWp, int n_sms, bool wide, int cpw) {
   if (wide) return mode == GSS_MODE_ALLF ? grid_for<GSS_MODE_ALLF, 1, true>(n_sms) : grid_for<GSS_MODE_TRIGGER, 1, true>(n_sms);
+#define GSS_GRID(M, A) (cpw == 16 ? grid_for<M, A, false, 16>(n_sms) : grid_for<M, A, false, 32>(n_sms))
   if (mode == GSS_MODE_ALLF) {
-    if (AWp == 1) return grid_for<GSS_MODE_ALLF, 1>(n_sms);
-    if (AWp == 2) return grid_for<GSS_MODE_ALLF, 2>(n_sms);
-    return grid_for<GSS_MODE_ALLF, 4>(n_sms);
+    if (AWp == 1) return GSS_GRID(GSS_MODE_ALLF, 1);
+    if (AWp == 2) return GSS_GRID(GSS_MODE_ALLF, 2);
+    return GSS_GRID(GSS_MODE_ALLF, 4);
   }
-  if (AWp == 1) return grid_for<GSS_MODE_TRIGGER, 1>(n_sms);
-  if (AWp == 2) return grid_for<GSS_MODE_TRIGGER, 2>(n_sms);
-  return grid_for<GSS_MODE_TRIGGER, 4>(n_sms);
+  if (AWp == 1) return GSS_GRID(GSS_MODE_TRIGGER, 1);
+  if (AWp == 2) return GSS_GRID(GSS_MODE_TRIGGER, 2);
+  return GSS_GRID(GSS_MODE_TRIGGER, 4);
+#undef GSS_GRID
 }
 
 cudaError_t debug_bounds_errors(unsigned long long* out, bool reset) {

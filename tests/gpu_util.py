@@ -4,12 +4,13 @@ import numpy as np
 import paper_2012_03119_gb300 as gss
 
 
-def gpu_records(inst, mode=gss.GSS_MODE_ALLF, report_capacity=None, max_assignments=None, codes=None):
+def gpu_records(inst, mode=gss.GSS_MODE_ALLF, report_capacity=None, max_assignments=None, codes=None,
+                clauses_per_tile=0):
     codes = inst.codes if codes is None else codes
     N = codes.shape[0]
     cap = report_capacity or max(1024, inst.n_clauses * max(1, (N + 31) // 32))  # one record per (clause, word) at most
     with gss.Context(inst.n_vars, report_capacity=cap, max_assignments=max_assignments or max(N, 1),
-                     mode=mode) as ctx:
+                     mode=mode, clauses_per_tile=clauses_per_tile) as ctx:
         ctx.add_clauses(inst.offsets, inst.lits)
         ctx.set_assignments(codes)
         ctx.test()

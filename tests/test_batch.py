@@ -125,7 +125,8 @@ with gss.Batch() as b:
     same = all(np.array_equal(gss.expand_reports(b.fetch_reports(i)), oracle.allf_pairs(I.offsets, I.lits, I.codes))
                for i, I in enumerate(insts))
     info = b.info()
-print(json.dumps({"same": same, "tuned_us": info["tuned_test_us"], "grab": info["tiles_per_steal"]}))
+print(json.dumps({"same": same, "tuned_us": info["tuned_test_us"], "grab": info["tiles_per_steal"],
+                  "cpw": info["clauses_per_tile"]}))
 """
     cache = tmp_path / "tune.txt"
     env = dict(os.environ, GSS_AUTOTUNE_CACHE=str(cache))
@@ -136,5 +137,13 @@ print(json.dumps({"same": same, "tuned_us": info["tuned_test_us"], "grab": info[
         runs.append(json.loads(r.stdout.strip().splitlines()[-1]))
     assert runs[0]["same"] and runs[1]["same"]
     assert runs[0]["tuned_us"] > 0 and runs[1]["tuned_us"] == 0
-    assert runs[1]["grab"] == runs[0]["grab"]
+    assert runs[1]["grab"] == runs[0]["grab"] and runs[1]["cpw"] == runs[0]["cpw"]
     assert len(cache.read_text().split("\n")) >= 2
+    # the cache file also fixes the tile shape: both shapes give the oracle's records
+    lines = [l.split() for l in cache.read_text().splitlines() if l.strip()]
+    for cpw in (16, 32):
+        cache.write_text("".join(f"{k} {g} {d} {cpw}\n" for k, g, d, _ in lines))
+        r = subprocess.run([sys.executable, "-c", script, root], env=env, capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0, r.stderr[-2000:]
+        out = json.loads(r.stdout.strip().splitlines()[-1])
+        assert out["same"] and out["tuned_us"] == 0 and set(out["cpw"]) == {cpw}

@@ -68,7 +68,30 @@ def test_independent_assignments_many_hits():
     assert len(assert_parity(inst)) > 10000
 
 
-def test_sizes_around_head_width_and_tautologies():
+@pytest.mark.parametrize("cpw", [16, 32])
+@pytest.mark.parametrize("mode", [ALLF, TRIG])
+@pytest.mark.parametrize("law", ["geom", "lognormal"])
+def test_tile_shapes(cpw, mode, law):
+    """Both test tile shapes (a lane per clause; two lanes per clause, whose segment results
+    compose) give the oracle's pairs and the oracle's aggregate-test count: short and long
+    clauses (CSR tails of several 16-literal rounds), a ragged last tile (3001 clauses), a
+    ragged last group (200 assignments)."""
+    inst = small_instance(n_vars=700, n_clauses=3001, n_assign=200, seed=21, law=law, cap=200)
+    assert_parity(inst, mode, clauses_per_tile=cpw)
+    with gss.Context(inst.n_vars, mode=mode, report_capacity=1 << 20, max_assignments=200,
+                     clauses_per_tile=cpw) as ctx:
+        ctx.add_clauses(inst.offsets, inst.lits)
+        ctx.run(inst.codes)
+        st = gss.gss_get_stats(ctx.ptr)
+    assert st["candidate_pairs"] == len(oracle.aggregate_pairs(inst.offsets, inst.lits, inst.codes, mode=mode))
+
+
+@pytest.mark.parametrize("cpw", [16, 32])
+def test_tile_shapes_around_head_width(cpw):
+    test_sizes_around_head_width_and_tautologies(cpw)
+
+
+def test_sizes_around_head_width_and_tautologies(cpw=0):
     V, rng = 40, np.random.default_rng(1)
     clauses = []
     for s in list(range(1, 21)) * 30:
@@ -84,8 +107,8 @@ def test_sizes_around_head_width_and_tautologies():
     lits = np.array([l for c in clauses for l in c], np.uint32)
     codes = synth.assign_trail(V, 512, 0.5, 1.0, 9)
     inst = synth.Instance("heads", V, off, lits, codes, np.zeros((0, 2), np.uint32))
-    assert_parity(inst, ALLF)
-    assert_parity(inst, TRIG)
+    assert_parity(inst, ALLF, clauses_per_tile=cpw)
+    assert_parity(inst, TRIG, clauses_per_tile=cpw)
 
 
 def test_all_u_assignments():
@@ -175,6 +198,19 @@ def test_invalid_inputs_leave_state_unchanged():
         assert ei.value.code == gss.GSS_E_INVAL
         after = ctx.run(inst.codes)
         assert np.array_equal(gss.expand_reports(before), gss.expand_reports(after))
+
+
+@pytest.mark.parametrize("layout", [gss.GSS_LAYOUT_FREQUENCY, gss.GSS_LAYOUT_IDENTITY])
+def test_assignments_before_the_first_clauses(layout):
+    """An assignment set given before any clause: the frequency layout's numbering, fixed by
+    the first clause batch, applies to it as well."""
+    inst = small_instance()
+    with gss.Context(inst.n_vars, max_assignments=inst.n_assign, layout=layout) as ctx:
+        ctx.set_assignments(inst.codes)
+        ctx.add_clauses(inst.offsets, inst.lits)
+        ctx.test()
+        got = gss.expand_reports(ctx.fetch_reports())
+    assert np.array_equal(got, oracle.allf_pairs(inst.offsets, inst.lits, inst.codes))
 
 
 def test_test_before_assignments():

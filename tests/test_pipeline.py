@@ -1,0 +1,98 @@
+"""Two plane sets (pipeline = 2): the packing of the next assignment set runs on its own
+stream while the last set's test runs.  Records must be those of each set alone, whatever
+the interleaving of set / test / fetch calls."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2012_03119_gb300 as gss
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def sets_for(inst, k, seed0=100):
+    out = [inst.codes]
+    for i in range(1, k):
+        out.append(synth.assign_trail(inst.n_vars, inst.n_assign, 0.3, 0.7, seed0 + i))
+    return out
+
+
+@pytest.mark.parametrize("mode", [gss.GSS_MODE_ALLF, gss.GSS_MODE_TRIGGER])
+def test_interleaved_sets_equal_each_set_alone(mode):
+    import torch
+    inst = synth.single(scale=0.01)  # 10k vars, 40k clauses, 1024 trail assignments
+    sets = sets_for(inst, 5)
+    want = [oracle.pairs(inst.offsets, inst.lits, c, mode) for c in sets]
+    d_sets = [torch.from_numpy(c).cuda() for c in sets]
+    cap = inst.n_clauses * 32 + 1024
+    with gss.Context(inst.n_vars, max_assignments=1024, report_capacity=cap, mode=mode, pipeline=2) as ctx:
+        ctx.add_clauses(inst.offsets, inst.lits)
+        torch.cuda.synchronize()
+        # set k + 1 is given (packed on the second stream) before set k's records are read
+        ctx.set_assignments(d_sets[0])
+        for k in range(len(sets)):
+            ctx.test()
+            if k + 1 < len(sets):
+                ctx.set_assignments(d_sets[k + 1] if k % 2 else sets[k + 1])  # device and host sets alternate
+            got = gss.expand_reports(ctx.fetch_reports())
+            np.testing.assert_array_equal(got, want[k])
+        # and again in the plain order
+        for k in range(len(sets)):
+            np.testing.assert_array_equal(gss.expand_reports(ctx.run(sets[k])), want[k])
+
+
+def test_second_set_without_test_drops_the_last_results():
+    """Two sets in a row after a test: the second reuses the tested plane set, so the last
+    test's results are gone (GSS_E_STATE), and the next test reads the newest set."""
+    inst = synth.single(scale=0.005)
+    a, b, c = sets_for(inst, 3)
+    with gss.Context(inst.n_vars, max_assignments=1024, report_capacity=1 << 22, pipeline=2) as ctx:
+        ctx.add_clauses(inst.offsets, inst.lits)
+        ctx.set_assignments(a)
+        ctx.test()
+        ctx.set_assignments(b)
+        np.testing.assert_array_equal(gss.expand_reports(ctx.fetch_reports()),
+                                      oracle.allf_pairs(inst.offsets, inst.lits, a))
+        ctx.set_assignments(c)
+        ctx.test()
+        np.testing.assert_array_equal(gss.expand_reports(ctx.fetch_reports()),
+                                      oracle.allf_pairs(inst.offsets, inst.lits, c))
+        ctx.set_assignments(a)
+        ctx.set_assignments(b)
+        with pytest.raises(gss.GssError) as ei:
+            ctx.fetch_reports()
+        assert ei.value.code == gss.GSS_E_STATE
+        ctx.test()
+        np.testing.assert_array_equal(gss.expand_reports(ctx.fetch_reports()),
+                                      oracle.allf_pairs(inst.offsets, inst.lits, b))
+
+
+def test_pipelined_wide_sets_and_stats():
+    """Sets above 4096 assignments (second aggregate level) through two plane sets, and the
+    statistics of the last test while the next set is being packed."""
+    V, N = 600, 5000
+    off = synth.offsets_from_sizes(synth.clause_sizes(3000, "geom", 1 / 7, 0, 30, V, 5))
+    lits = synth.clause_lits(off, V, 5)
+    s1 = synth.assign_trail(V, N, 0.3, 0.7, 5, group=1024, flip_frac=0.1)
+    s2 = synth.assign_trail(V, N - 333, 0.3, 0.7, 6, group=1024, flip_frac=0.1)
+    with gss.Context(V, max_assignments=N, report_capacity=1 << 20, pipeline=2) as ctx:
+        ctx.add_clauses(off, lits)
+        ctx.set_assignments(s1)
+        ctx.test()
+        ctx.set_assignments(s2)
+        got1 = gss.expand_reports(ctx.fetch_reports())
+        st = ctx.stats()
+        assert st["group_pairs"] == 3000 * ((N + 31) // 32)
+        want_groups = oracle.aggregate_pairs(off, lits, s1, group=32)
+        assert st["candidate_pairs"] == len(want_groups)
+        ctx.test()
+        got2 = gss.expand_reports(ctx.fetch_reports())
+    np.testing.assert_array_equal(got1, oracle.allf_pairs(off, lits, s1))
+    np.testing.assert_array_equal(got2, oracle.allf_pairs(off, lits, s2))
+
+
+def test_pipeline_config_checks():
+    with pytest.raises(gss.GssError) as ei:
+        gss.Context(100, pipeline=3)
+    assert ei.value.code == gss.GSS_E_INVAL

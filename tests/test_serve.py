@@ -93,6 +93,17 @@ def test_serve_alone_mixed_and_oracle(work, snaps):
             th.join()
         assert not errors, errors
         st = srv.stats()
+        # continuous batching: requests that arrive while a launch runs join the next one.  The
+        # mix above usually shows it; if its timing did not, bursts of back-to-back submissions do
+        final = len(work.offsets) - 1
+        for attempt in range(5):
+            if st["launches"] < st["words_launched"]:
+                break
+            ids = [(k, srv.submit(snaps[k], wait_us=10_000_000)) for k in range(8)]
+            for k, rid in ids:
+                rec, info = srv.wait(rid)
+                np.testing.assert_array_equal(gss.expand_reports(rec), prefix_oracle(work, info["watermark"], snaps[k]))
+            st = srv.stats()
 
     for i, _ in probes:
         np.testing.assert_array_equal(mixed[i], alone[i])
@@ -104,8 +115,8 @@ def test_serve_alone_mixed_and_oracle(work, snaps):
         assert (rec["word"] == 0).all()
         np.testing.assert_array_equal(gss.expand_reports(rec), prefix_oracle(work, wm, snaps[k]))
     assert st["committed_clauses"] == final
-    assert st["completed"] == st["submitted"] == 48 and st["dropped"] == 0
-    assert st["words_launched"] == 48
+    assert st["completed"] == st["submitted"] == st["words_launched"] and st["submitted"] % 8 == 0
+    assert st["submitted"] >= 48 and st["dropped"] == 0
     assert st["launches"] < st["words_launched"], "no launch carried more than one request"
     assert st["p99_us"] >= st["p50_us"] > 0
 
@@ -275,3 +286,95 @@ def test_serve_padding_never_counts_against_capacity(work):
         np.testing.assert_array_equal(a, w)
     assert st["completed"] == st["submitted"] and st["reports"] == st["completed"]
     assert batched, "no launch carried more than one request"
+
+
+@pytest.mark.parametrize("mode", [gss.GSS_MODE_ALLF, gss.GSS_MODE_TRIGGER])
+def test_serve_activity_and_reduce(work, snaps, mode):
+    """Section 3.6 on the server's resident database: each launch bumps the clauses it reports,
+    and a reduction removes the lowest-activity long clauses between launches.  Requests before
+    and after the reduction, and after more clauses arrive, equal the activity oracle's pairs
+    on its database; activities and ids match bit for bit; a watermark below the newest ids
+    keeps out the clauses added after it."""
+    from oracle.activity import ActivityOracle
+    ao = ActivityOracle(0.8)
+    ofn = oracle.trigger_pairs if mode == gss.GSS_MODE_TRIGGER else oracle.allf_pairs
+    with make_server(work, mode=mode, lanes=2, tests_in_flight=1) as srv:
+        srv.set_activity(0.8)
+        off0, lits0 = work.csr(0, work.n_initial)
+        assert srv.add_clauses(off0, lits0) == ao.add(off0, lits0) == 0
+
+        def request(k, watermark=None):
+            rec, info = srv.wait(srv.submit(snaps[k], watermark=watermark, wait_us=10_000_000))
+            got = gss.expand_reports(rec)
+            want = ao.pairs(snaps[k], mode)
+            if watermark is not None:
+                want = want[want[:, 0] < watermark]
+            np.testing.assert_array_equal(got, want)
+            ao.after_test(want[:, 0])  # one launch per request: one test for the bumps
+            return info
+
+        for k in range(4):
+            request(k)
+        n = srv.reduce(0.5)
+        assert n == ao.reduce(0.5) > 0
+        np.testing.assert_array_equal(srv.clause_ids(), ao.ids)
+        np.testing.assert_array_equal(srv.activity().view(np.uint32), ao.act.view(np.uint32))
+        for k in range(4, 7):
+            request(k)
+        off1, lits1 = work.csr(*work.batch_range(0))  # new clauses take new ids, never reused ones
+        first = srv.add_clauses(off1, lits1)
+        assert first == ao.add(off1, lits1) == work.n_initial
+        for k in range(7, 10):
+            request(k)
+        info = request(10, watermark=first)  # only the clauses committed before the new batch
+        assert info["watermark"] == first
+        np.testing.assert_array_equal(srv.clause_ids(), ao.ids)
+        np.testing.assert_array_equal(srv.activity().view(np.uint32), ao.act.view(np.uint32))
+        st = srv.stats()
+        assert st["reductions"] == 1 and st["clauses_removed"] == n
+        assert st["committed_clauses"] == ao.n_clauses and st["next_clause_id"] == ao.next_id
+
+
+def test_serve_reduce_while_requests_run(work, snaps):
+    """A reduction issued while clients submit: it waits for running launches, holds new ones,
+    and every request's records equal the oracle on the database before or after it."""
+    from oracle.activity import ActivityOracle
+    ao = ActivityOracle(1.0)
+    with make_server(work, lanes=3, tests_in_flight=1) as srv:
+        srv.set_activity(1.0)
+        off0, lits0 = work.csr(0, work.n_initial)
+        srv.add_clauses(off0, lits0)
+        ao.add(off0, lits0)
+        before = [ao.pairs(s) for s in snaps[:8]]
+        results, errors = [], []
+
+        def client():
+            try:
+                ids = [(k, srv.submit(snaps[k], wait_us=10_000_000)) for k in range(8) for _ in range(3)]
+                results.extend((k, srv.wait(rid)[0]) for k, rid in ids)
+            except Exception as e:  # reported below
+                errors.append(e)
+
+        th = threading.Thread(target=client)
+        th.start()
+        time.sleep(0.001)
+        removed = srv.reduce(0.3)
+        th.join()
+        assert not errors, errors
+        assert removed > 0
+        kept = set(srv.clause_ids().tolist())
+        for k, rec in results:
+            got = gss.expand_reports(rec)
+            after = before[k][np.isin(before[k][:, 0], np.array(sorted(kept), np.uint32))]
+            assert np.array_equal(got, before[k]) or np.array_equal(got, after)
+        assert srv.stats()["completed"] == 24
+
+
+def test_serve_activity_needs_one_test_in_flight(work):
+    with make_server(work, lanes=2, tests_in_flight=2) as srv:
+        with pytest.raises(gss.GssError) as ei:
+            srv.set_activity(0.9)
+        assert ei.value.code == gss.GSS_E_STATE
+        with pytest.raises(gss.GssError) as ei:
+            srv.reduce(0.5)
+        assert ei.value.code == gss.GSS_E_STATE
