@@ -509,6 +509,15 @@ def run_serve(args):
     return out
 
 
+def child_summary(argv: list[str], summarise) -> dict:
+    """Run bench.py with argv in a child process and summarise its JSON line."""
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), *argv], capture_output=True, text=True, timeout=900)
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    if r.returncode != 0 or not lines:
+        return {"error": f"bench.py {' '.join(argv)} exited {r.returncode}: {r.stderr[-500:]}"}
+    return summarise(json.loads(lines[-1]))
+
+
 def batch_summary(b: dict) -> dict:
     """The batching line's figures that the default line carries."""
     return {"workload": b["config"]["workload"], "value": b["value"], "unit": b["unit"],
@@ -521,7 +530,8 @@ def serve_summary(v: dict) -> dict:
     """The serving line's figures that the default line carries."""
     ol = v["open_loop"]
     return {"workload": v["config"]["workload"], "value": v["value"], "unit": v["unit"],
-            "latency_us": ol["latency_us"], "requests": ol["requests"], "dropped": ol["dropped"],
+            "latency_us": ol["latency_us"], "latency_parts_us": ol["latency_parts_us"],
+            "requests": ol["requests"], "dropped": ol["dropped"],
             "mean_batch_words": ol["mean_batch_words"], "saturated": v["saturated"],
             "one_launch_per_request": v["one_launch_per_request"],
             "speedup_vs_one_launch_per_request": v["speedup_vs_one_launch_per_request"],
@@ -780,13 +790,15 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(inst)
     if world == 1 and args.config == "single" and args.scale == 1.0 and args.mode == "allf" and not args.no_extras:
-        # the batching and serving workloads, on the same GPU, so that one run records every form
+        # the batching and serving workloads on the same GPU, so that one run records every form;
+        # each in a process of its own, as when run alone (a process that already ran the other
+        # workloads carries their Python objects, and its garbage collector pauses the
+        # simulated solver threads)
         del inst
         torch.cuda.empty_cache()
-        bargs = argparse.Namespace(**{**vars(args), "steps": min(args.steps, 20), "warmup": 3})
-        out["batch"] = batch_summary(run_batch(bargs))
-        torch.cuda.empty_cache()
-        out["serve"] = serve_summary(run_serve(bargs))
+        steps = str(min(args.steps, 20))
+        out["batch"] = child_summary(["--config", "batch", "--steps", steps, "--warmup", "3"], batch_summary)
+        out["serve"] = child_summary(["--config", "serve"], serve_summary)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
