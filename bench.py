@@ -11,8 +11,9 @@ read back their count.  value = clauses x assignments tested per second (G/s).
 e2e: the same step through the public API from pinned HOST memory: the codes go
 host->device inside the timed region and the records come back device->host.  The
 context keeps two plane sets, so step k + 1's codes cross the host link while step k's
-test runs; the line also carries the host link's copy rate, measured in the same run, and
-the fraction of the bound it sets that e2e reaches.
+test runs and its records travel back (gss_fetch_reports_async); the line also carries
+the host link's copy rate, measured in the same run, and the fraction of the bound it
+sets that e2e reaches.
 
 --impl reference runs the oracle (plain C on the host cores) on a bounded sample of
 the same workload, the reference arm of this comparison.
@@ -714,13 +715,14 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     # every step copies its codes in and its records out; with two plane sets the codes of step
-    # k + 1 cross the host link while step k's test runs, before step k's records are read
+    # k + 1 cross the host link while step k's test runs and its records travel back
     ctx.set_assignments(h_codes.numpy())
     for k in range(e2e_steps):
         ctx.test()
+        ctx.fetch_reports_async(h_rec)
         if k + 1 < e2e_steps:
             ctx.set_assignments(h_codes.numpy())
-        ctx.fetch_reports(h_rec)
+        ctx.fetch_wait()
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s, dist)
     # the host link measured in the same run: the step's codes, pinned host -> device, one copy

@@ -236,6 +236,21 @@ int gss_test(gss_ctx* ctx);
 int gss_fetch_reports(gss_ctx* ctx, gss_report* out, uint64_t cap, uint64_t* n_out);
 
 /*
+ * The same copy without waiting: queue, on the context's stream after the last gss_test, a
+ * kernel that writes min(records, cap) records straight into `out`, and return at once.
+ * `out` must be memory the GPU can write: pinned host memory (cudaMallocHost /
+ * cudaHostAlloc / cudaHostRegister), device or managed memory, or pageable host memory on a
+ * device that can access it (GSS_E_INVAL otherwise); it must stay valid until
+ * gss_fetch_wait returns.  gss_fetch_wait synchronises the stream and returns as
+ * gss_fetch_reports would (*n_out: all the test's records; GSS_E_OVERFLOW, GSS_E_INVAL,
+ * GSS_E_TIMEOUT likewise).  A caller that sets the next assignment set between the two calls
+ * (two plane sets, gss_config.pipeline = 2) moves the records back while the next set's
+ * codes come in.  GSS_E_STATE: no test to fetch / nothing to wait for.
+ */
+int gss_fetch_reports_async(gss_ctx* ctx, gss_report* out, uint64_t cap);
+int gss_fetch_wait(gss_ctx* ctx, uint64_t* n_out);
+
+/*
  * As gss_fetch_reports but copies nothing: waits for the last test and
  * returns its record count.  The records stay in device memory, readable
  * through gss_reports_device().

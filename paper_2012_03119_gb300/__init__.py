@@ -135,6 +135,8 @@ SIGNATURES = {
     "gss_server_wait": (i32, [P, u64, ctypes.c_int64, P, u64, P, P]),
     "gss_server_get_stats": (i32, [P, P]),
     "gss_server_last_error": (ctypes.c_char_p, [P]),
+    "gss_fetch_reports_async": (i32, [P, P, u64]),
+    "gss_fetch_wait": (i32, [P, P]),
     "gss_server_set_activity": (i32, [P, ctypes.c_float]),
     "gss_server_reduce": (i32, [P, ctypes.c_double, P]),
     "gss_server_get_activity": (i32, [P, P, u64, P]),
@@ -352,6 +354,20 @@ class Context:
 
     def fetch_reports(self, out=None) -> np.ndarray:
         return gss_fetch_reports(self.ptr, out)
+
+    def fetch_reports_async(self, out: np.ndarray) -> None:
+        """Queue the copy of the last test's records into ``out`` (REPORT_DTYPE, memory the GPU
+        can write, e.g. a numpy view of pinned memory); ``fetch_wait`` finishes it."""
+        assert out.dtype == REPORT_DTYPE and out.flags["C_CONTIGUOUS"]
+        self._fetch_out = out
+        _check(self.ptr, load().gss_fetch_reports_async(self.ptr, ctypes.c_void_p(out.ctypes.data), len(out)))
+
+    def fetch_wait(self) -> np.ndarray:
+        """Wait for fetch_reports_async; returns the records (a view of its buffer)."""
+        n = ctypes.c_uint64()
+        _check(self.ptr, load().gss_fetch_wait(self.ptr, ctypes.byref(n)))
+        out, self._fetch_out = self._fetch_out, None
+        return out[: n.value]
 
     def set_report_capacity(self, cap: int) -> None:
         gss_set_report_capacity(self.ptr, cap)

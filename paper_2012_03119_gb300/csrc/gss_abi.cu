@@ -578,6 +578,54 @@ int gss_fetch_reports(gss_ctx* c, gss_report* out, uint64_t cap, uint64_t* n_out
   return GSS_OK;
 }
 
+int gss_fetch_reports_async(gss_ctx* c, gss_report* out, uint64_t cap) {
+  TraceRange tr("gss_fetch_reports_async");
+  if (!c || (cap && !out)) return c ? fail(c, GSS_E_INVAL, "out is NULL") : GSS_E_INVAL;
+  c->err.clear();
+  if (!c->tested) return fail(c, GSS_E_STATE, "no gss_test to fetch");
+  DeviceGuard dg(c->device);
+  gss_report* dst = out;
+  if (cap) {  // the copy kernel writes out directly: it must be memory the GPU can write
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, out) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, GSS_E_INVAL, "out: not a pointer the runtime knows");
+    }
+    if (a.type == cudaMemoryTypeHost) {
+      if (!a.devicePointer) return fail(c, GSS_E_INVAL, "out: pinned host memory not mapped for the device");
+      dst = static_cast<gss_report*>(a.devicePointer);
+    } else if (a.type == cudaMemoryTypeUnregistered) {
+      int pageable = 0;
+      if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, c->device) != cudaSuccess || !pageable)
+        return fail(c, GSS_E_INVAL, "out: pageable host memory, which this device cannot write; pin it");
+    }
+  }
+  CK(c, launch_copy_records(c->rec, set_status(c, c->tested_set), c->rec_cap, cap, dst, 2 * c->n_sms, c->stream));
+  c->fetch_pending = true;
+  c->fetch_cap = cap;
+  return GSS_OK;
+}
+
+int gss_fetch_wait(gss_ctx* c, uint64_t* n_out) {
+  if (!c) return GSS_E_INVAL;
+  c->err.clear();
+  if (!c->fetch_pending) return fail(c, GSS_E_STATE, "no gss_fetch_reports_async to wait for");
+  c->fetch_pending = false;
+  DeviceGuard dg(c->device);
+  uint64_t n = 0;
+  int rc = wait_test(c, &n, true);  // synchronises the stream: the records have landed
+  if (n_out) *n_out = n;
+  if (rc) return rc;
+  if (n > c->rec_cap)
+    return fail(c, GSS_E_OVERFLOW, "device report buffer overflowed: %llu records > capacity %llu; "
+                "raise it with gss_set_report_capacity and re-run gss_test",
+                (unsigned long long)n, (unsigned long long)c->rec_cap);
+  if (n > c->fetch_cap)
+    return fail(c, GSS_E_OVERFLOW, "%llu records > caller capacity %llu", (unsigned long long)n,
+                (unsigned long long)c->fetch_cap);
+  return GSS_OK;
+}
+
 int gss_report_count(gss_ctx* c, uint64_t* n_out) {
   if (!c || !n_out) return GSS_E_INVAL;
   c->err.clear();

@@ -81,6 +81,8 @@ struct gss_ctx {
   DevStatus* st = nullptr;    // [0]: pack + test of plane set 0, [1]: ingest, [2]: pack + test of plane set 1
   DevStatus* h_st = nullptr;  // pinned mirror
   bool tested = false;
+  bool fetch_pending = false;  // a gss_fetch_reports_async not yet waited for
+  uint64_t fetch_cap = 0;
   int grid[2][5][2] = {};     // cached persistent grid per (mode, AWp <= 4, tile shape 32 / 16)
   int grid_wide[2] = {0, 0};  // per mode, for sets of more than GSS_MAX_NARROW_ASSIGNMENTS
 

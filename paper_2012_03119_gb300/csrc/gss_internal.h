@@ -125,6 +125,11 @@ cudaError_t launch_test(int mode, const ClauseView& db, uint64_t c_lo, uint64_t 
                         const uint64_t* wm = nullptr, uint32_t n_wm = 0, const ActivityView& av = ActivityView{},
                         const WideView& wide = WideView{}, int cpw = 32);
 
+// Copy min(st->n_records, cap_dev, cap_out) records to out (device memory, or host memory the
+// GPU can write), on stream s after the test that made them.
+cudaError_t launch_copy_records(const gss_report* rec, const DevStatus* st, uint64_t cap_dev, uint64_t cap_out,
+                                gss_report* out, int grid, cudaStream_t s);
+
 // Group a serving launch's records by plane word (request) into out: records of word w at
 // [sum of count[0..w), + count[w]), their mask ANDed with nmask[w], records left without a bit
 // dropped, word set to 0.  count / cursor: 32 device counters each (zeroed here); out holds

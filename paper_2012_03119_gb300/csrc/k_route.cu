@@ -6,7 +6,8 @@
 // assignments (rows past a request's own assignments are U), drops records left without
 // a bit and writes word 0 (the request's own word).  Two grid-stride passes: a per-word
 // count, then a scatter behind per-word cursors; the destination may be mapped host memory,
-// so results reach the host without a second copy.
+// so results reach the host without a second copy.  k_copy_records moves a context's records
+// the same way (gss_fetch_reports_async).
 #include "gss_internal.h"
 
 namespace gss {
@@ -85,7 +86,29 @@ __global__ void __launch_bounds__(RT_THREADS) k_route_scatter(const gss_report* 
   }
 }
 
+// Copy min(records of the test, cap_dev, cap_out) records into out, which may be host memory
+// the GPU can write (pinned or mapped): the records travel as the copy runs, on the test's
+// stream, with no device-to-host copy call that would need the count first.
+__global__ void __launch_bounds__(RT_THREADS) k_copy_records(const uint32_t* __restrict__ rec,
+                                                             const DevStatus* __restrict__ st, uint64_t cap_dev,
+                                                             uint64_t cap_out, uint32_t* __restrict__ out) {
+  uint64_t n = st->n_records;
+  if (n > cap_dev) n = cap_dev;
+  if (n > cap_out) n = cap_out;
+  const uint64_t words = 3ull * n;
+  for (uint64_t i = (uint64_t)blockIdx.x * RT_THREADS + threadIdx.x; i < words; i += (uint64_t)gridDim.x * RT_THREADS)
+    out[i] = __ldg(rec + i);
+}
+
 }  // namespace
+
+cudaError_t launch_copy_records(const gss_report* rec, const DevStatus* st, uint64_t cap_dev, uint64_t cap_out,
+                                gss_report* out, int grid, cudaStream_t s) {
+  if (cap_out == 0) return cudaSuccess;
+  k_copy_records<<<grid, RT_THREADS, 0, s>>>(reinterpret_cast<const uint32_t*>(rec), st, cap_dev, cap_out,
+                                             reinterpret_cast<uint32_t*>(out));
+  return cudaGetLastError();
+}
 
 cudaError_t launch_route(const gss_report* rec, const DevStatus* st, uint64_t cap, const uint32_t* nmask, uint32_t k,
                          unsigned long long* count, unsigned long long* cursor, gss_report* out, int grid,

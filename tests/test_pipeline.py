@@ -96,3 +96,44 @@ def test_pipeline_config_checks():
     with pytest.raises(gss.GssError) as ei:
         gss.Context(100, pipeline=3)
     assert ei.value.code == gss.GSS_E_INVAL
+
+
+def test_async_fetch():
+    """gss_fetch_reports_async writes the records into the caller's buffer on the stream, so
+    the next set can be given before they are waited for; the results equal gss_fetch_reports,
+    overflow reports the full count, and a buffer the GPU cannot write is refused."""
+    import torch
+    inst = synth.single(scale=0.005)
+    a, b = sets_for(inst, 2)
+    want_a = oracle.allf_pairs(inst.offsets, inst.lits, a)
+    want_b = oracle.allf_pairs(inst.offsets, inst.lits, b)
+    cap = 1 << 20
+    pinned = torch.empty(cap * 12, dtype=torch.uint8).pin_memory().numpy().view(gss.REPORT_DTYPE)
+    with gss.Context(inst.n_vars, max_assignments=1024, report_capacity=cap, pipeline=2) as ctx:
+        ctx.add_clauses(inst.offsets, inst.lits)
+        with pytest.raises(gss.GssError) as ei:
+            ctx.fetch_wait()
+        assert ei.value.code == gss.GSS_E_STATE
+        ctx.set_assignments(a)
+        ctx.test()
+        ctx.fetch_reports_async(pinned)
+        ctx.set_assignments(b)  # set b's copy and packing while set a's records travel
+        np.testing.assert_array_equal(gss.expand_reports(ctx.fetch_wait()), want_a)
+        ctx.test()
+        ctx.fetch_reports_async(pinned)
+        np.testing.assert_array_equal(gss.expand_reports(ctx.fetch_wait()), want_b)
+        n_all = ctx.report_count()
+        ctx.fetch_reports_async(pinned[:5])  # too small: the first 5 records, the full count
+        with pytest.raises(gss.GssError) as ei:
+            ctx.fetch_wait()
+        assert ei.value.code == gss.GSS_E_OVERFLOW and n_all > 5
+        part = gss.expand_reports(pinned[:5])
+        assert set(map(tuple, part.tolist())) <= set(map(tuple, want_b.tolist()))
+        # pageable memory: written where the device can reach it, refused where it cannot
+        pageable = np.zeros(cap, gss.REPORT_DTYPE)
+        try:
+            ctx.fetch_reports_async(pageable)
+        except gss.GssError as e:
+            assert e.code == gss.GSS_E_INVAL
+        else:
+            np.testing.assert_array_equal(gss.expand_reports(ctx.fetch_wait()), want_b)
