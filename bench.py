@@ -81,8 +81,9 @@ class ClockSampler:
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, interval_ms: int = 100):
         self.gpu = gpu_index
+        self.interval_ms = interval_ms
         self.proc = None
         # raw samples: BENCH_CLOCKS_DIR if set (to keep them), else the system's temporary directory
         out_dir = os.environ.get("BENCH_CLOCKS_DIR") or tempfile.gettempdir()
@@ -93,7 +94,7 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.gpu), "-lms", "100"], stdout=self.f,
+                                          "-i", str(self.gpu), "-lms", str(self.interval_ms)], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -416,7 +417,7 @@ def run_serve(args):
         except Exception as e:
             errors.append(e)
 
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(0, args.serve_clock_ms)
     clocks.start()
     s0 = srv.stats()
     ths = [threading.Thread(target=ingest)] + [threading.Thread(target=client, args=(t,)) for t in range(n_threads)]
@@ -557,6 +558,8 @@ def main():
     ap.add_argument("--serve-threads", type=int, default=32)
     ap.add_argument("--serve-sat-requests", type=int, default=1024)
     ap.add_argument("--serve-tests-in-flight", type=int, default=1)
+    ap.add_argument("--serve-clock-ms", type=int, default=100,
+                    help="nvidia-smi sampling interval during the serving run")
     ap.add_argument("--mode", default="allf", choices=["allf", "trigger"],
                     help="what a pair reports: all literals F (default) or Definition 'triggers'")
     ap.add_argument("--overlap", action="store_true",

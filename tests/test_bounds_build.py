@@ -1,5 +1,6 @@
 """The bounds-checked build (GSS_DEBUG_BOUNDS=1): the same results as the oracle on every path
-(plain test in both modes, wide sets in both modes, batch, serving, activity and deletion),
+(plain test in both modes and both tile shapes, wide sets in both modes, batch, serving with
+and without a reduction, activity and deletion),
 with no out-of-range gather counted.  Runs in a subprocess that builds and loads the checked
 library, so the rest of the suite keeps the release build."""
 import json
@@ -62,6 +63,27 @@ for mode in (gss.GSS_MODE_ALLF, gss.GSS_MODE_TRIGGER):  # more than 4096 assignm
         ctx.add_clauses(woff, wlits)
         got = gss.expand_reports(ctx.run(wcodes))
     ok["wide%d" % mode] = bool(np.array_equal(got, oracle.pairs(woff, wlits, wcodes, mode)))
+# the 16-clause tile shape (two lanes per clause), long clauses with CSR tails
+lsizes = synth.clause_sizes(900, "lognormal", 20.0, 1.0, 120, 500, 8)
+loff = synth.offsets_from_sizes(lsizes)
+llits = synth.clause_lits(loff, 500, 8)
+lcodes = synth.assign_trail(500, 200, 0.3, 0.7, 8)
+for mode in (gss.GSS_MODE_ALLF, gss.GSS_MODE_TRIGGER):
+    with gss.Context(500, mode=mode, report_capacity=1 << 20, max_assignments=200, clauses_per_tile=16) as ctx:
+        ctx.add_clauses(loff, llits)
+        got = gss.expand_reports(ctx.run(lcodes))
+    ok["cpw16_%d" % mode] = bool(np.array_equal(got, oracle.pairs(loff, llits, lcodes, mode)))
+# serving with activity and a reduction, then a request on the compacted database
+with gss.Server(w.n_vars, max_clauses=len(w.offsets), max_lits=int(w.offsets[-1]) + 1, slots=4, lanes=2) as srv:
+    srv.set_activity(0.9)
+    srv.add_clauses(*w.csr(0, w.n_initial))
+    srv.wait(srv.submit(snap, wait_us=10_000_000))
+    srv.reduce(0.5)
+    kept = srv.clause_ids()
+    rec, info = srv.wait(srv.submit(snap, wait_us=10_000_000))
+off = w.offsets[: w.n_initial + 1]
+sfull = oracle.allf_pairs(off, w.lits[: int(off[-1])], snap)
+ok["serve_reduce"] = bool(np.array_equal(gss.expand_reports(rec), sfull[np.isin(sfull[:, 0], kept)]))
 enabled, errors = gss.gss_debug_bounds()
 print(json.dumps({"ok": ok, "enabled": enabled, "errors": errors}))
 """
