@@ -222,5 +222,8 @@ int gss_oracle_aggregate_test(int mode, const uint64_t* off, const uint32_t* lit
       if (g & 2) ++n_f;
     }
   }
+#if ORACLE_MUTANT == 8 /* aggregate trigger threshold off by one */
+  return mode == MODE_ALLF ? 1 : (n_f + 2 >= s);
+#endif
   return mode == MODE_ALLF ? 1 : (n_f + 1 >= s);
 }

@@ -79,7 +79,7 @@ def test_empty_inputs():
 # Deliberately wrong oracle builds: each must be rejected by at least one pin.
 MUTANTS = {1: "wrong sign convention", 2: "drops last literal", 3: "treats U as F",
            4: "skips first literal", 5: "exists instead of for-all", 6: "trigger threshold off by one",
-           7: "aggregate all-F takes F or U in G(l)"}
+           7: "aggregate all-F takes F or U in G(l)", 8: "aggregate trigger threshold off by one"}
 
 
 @pytest.mark.parametrize("mutant", sorted(MUTANTS))
@@ -94,13 +94,15 @@ def test_pins_reject_mutant(mutant, tiny_instance):
     assert fails, f"mutant {mutant} ({MUTANTS[mutant]}) passed every pin"
 
 
-def test_aggregate_allf_mutant_is_caught_by_the_set_pin_alone():
-    """Mutant 7 changes only the all-F aggregate test, which the Theorem of Section 4.2 cannot
-    see (it only rules out false negatives): the two-sided pin rejects it by itself, while the
-    Theorem still holds for it."""
+@pytest.mark.parametrize("mutant,mode", [(7, 0), (8, 1)])
+def test_aggregate_mutant_is_caught_by_the_set_pin_alone(mutant, mode):
+    """Mutants 7 and 8 loosen only an aggregate test (all-F, trigger), which the Theorem of
+    Section 4.2 cannot see (it only rules out false negatives): the two-sided pin rejects each
+    by itself, while the Theorem still holds for it."""
     inst = synth.tiny()
-    assert pin_aggregate_theorem(inst, oracle.MODE_ALLF, group=8, mutant=7, max_clauses=500) == []
-    assert pin_aggregate_brute_force(2, mutant=7) != []
+    m = oracle.MODE_ALLF if mode == 0 else oracle.MODE_TRIGGER
+    assert pin_aggregate_theorem(inst, m, group=8, mutant=mutant, max_clauses=500) == []
+    assert pin_aggregate_brute_force(2, mutant=mutant) != []
 
 
 # ---------------------------------------------------------------- clause activity (Section 3.6)
