@@ -563,7 +563,7 @@ def main():
     ap.add_argument("--mode", default="allf", choices=["allf", "trigger"],
                     help="what a pair reports: all literals F (default) or Definition 'triggers'")
     ap.add_argument("--overlap", action="store_true",
-                    help="issue step k+1's packing before step k's count is read, beside step k's test")
+                    help="run step k+1's packing beside step k's test (default: queued behind it)")
     ap.add_argument("--layout", default="frequency", choices=["frequency", "identity"],
                     help="internal variable numbering of the clause database")
     args = ap.parse_args()
@@ -660,9 +660,12 @@ def main():
     def timed_steps(n_steps: int):
         """n_steps steps: pack step k's set, test it, read its record count back to the host.
         Packing and testing take turns (each kernel fills the GPU; running them side by side
-        measured slower); with --overlap, step k + 1's packing is issued before step k's count
-        is read, so that it runs beside step k's test.  Each kernel is bracketed by CUDA events
-        on the stream it runs on (after its wait for the other stream)."""
+        measured slower): step k + 1's packing (into the other plane set) is queued on the pack
+        stream behind step k's test before the host waits for step k's count, so the GPU does
+        not sit idle while the count travels to the host and the next launch is made.  With
+        --overlap, step k + 1's packing does not wait for step k's test and runs beside it.
+        Each kernel is bracketed by CUDA events on the stream it runs on (after its wait for
+        the other stream)."""
         evp = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(n_steps)]
         evt = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(n_steps)]
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -683,11 +686,11 @@ def main():
             evt[k][0].record(stream)
             ctx.test()
             evt[k][1].record(stream)
-            if args.overlap and k + 1 < n_steps:
-                pack(k + 1)  # runs beside step k's test
-            ctx.report_count()  # step k's result (record count) read back to the host
-            if not args.overlap and k + 1 < n_steps:
+            if k + 1 < n_steps:
+                if not args.overlap:
+                    pack_stream.wait_event(evt[k][1])  # in turn with step k's test
                 pack(k + 1)
+            ctx.report_count()  # step k's result (record count) read back to the host
         end.record(stream)
         torch.cuda.synchronize()
         if dist:
