@@ -99,9 +99,13 @@ typedef struct {
  * next set's host copy and packing proceed while the last test runs.  (On GB300 the packing
  * and test kernels each fill the GPU: running them side by side was measured slower than
  * running them in turn, so the gain is in hiding host copies and host round trips.)
+ * Host values are copied into a staging buffer of the plane set they go to, on a copy
+ * stream of the context's own, so that a set's copy does not wait for the last set's
+ * packing: the host link can stay busy from one set to the next.
  * Results are the same as with pipeline = 1.  Ordering: packing is not ordered after work
  * queued on `stream`; device codes written by other work must be complete before the
- * call (or ordered onto pack_stream by the caller).  Twice the plane memory is held.
+ * call (or ordered onto pack_stream by the caller).  Twice the plane memory is held, and
+ * twice the staging memory once host values have gone to both sets.
  */
 
 /*

@@ -185,15 +185,18 @@ int launch_grid(gss_ctx* c, int mode, uint32_t AWp, int cpw) {
 void release(gss_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->pack_stream && c->pack_stream != c->stream) cudaStreamSynchronize(c->pack_stream);
+  if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
   while (!c->allocs.empty()) dev_free(c, c->allocs.begin()->first);
   if (c->h_st) cudaFreeHost(c->h_st);
   for (int b = 0; b < 2; ++b) {
     if (c->ev_packed[b]) cudaEventDestroy(c->ev_packed[b]);
     if (c->ev_tested[b]) cudaEventDestroy(c->ev_tested[b]);
+    if (c->ev_staged[b]) cudaEventDestroy(c->ev_staged[b]);
   }
   if (c->ev_copied) cudaEventDestroy(c->ev_copied);
 
   if (c->own_pack_stream && c->pack_stream) cudaStreamDestroy(c->pack_stream);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -266,9 +269,14 @@ int gss_create(gss_ctx** out, uint32_t n_vars, const gss_config* cfg_in) {
     } else {
       c->own_pack_stream = true;
     }
+    if (!rc && cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      c->copy_stream = nullptr;
+      rc = GSS_E_CUDA;
+    }
     for (int b = 0; b < 2 && !rc; ++b)
       if (cudaEventCreateWithFlags(&c->ev_packed[b], cudaEventDisableTiming) != cudaSuccess ||
-          cudaEventCreateWithFlags(&c->ev_tested[b], cudaEventDisableTiming) != cudaSuccess)
+          cudaEventCreateWithFlags(&c->ev_tested[b], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c->ev_staged[b], cudaEventDisableTiming) != cudaSuccess)
         rc = GSS_E_CUDA;
   }
   if (!rc && cudaEventCreateWithFlags(&c->ev_copied, cudaEventDisableTiming) != cudaSuccess) rc = GSS_E_CUDA;
@@ -416,25 +424,35 @@ int stage_assignments(gss_ctx* c, const uint8_t* src, uint64_t pitch, uint32_t n
   // the packing kernel reads codes with 2-D TMA boxes: rows 16-byte aligned
   const bool aligned = device_src && pitch % 16 == 0 && (reinterpret_cast<uintptr_t>(src) % 16) == 0;
   if (n && !aligned) {  // host data, or a device layout the packing kernel cannot read as 32-bit words
-    if (c->codes_rows < n) {
-      CK(c, cudaStreamSynchronize(ps));  // a packing of the other set may still read the old buffer
-      dev_free(c, c->codes);
-      c->codes = nullptr;
-      c->codes_rows = 0;
+    // pipeline 1: one staging buffer, the copy queued on the packing stream behind the packing
+    // that still reads it.  pipeline 2: set b's own buffer, copied on copy_stream once the last
+    // packing of set b has read it, and the packing waits for the copy.
+    gss_ctx::PlaneSet& q = c->sets[b];
+    cudaStream_t cs = c->pipeline == 2 ? c->copy_stream : ps;
+    if (q.codes_rows < n) {
+      CK(c, cudaStreamSynchronize(ps));  // a packing may still read the old buffer
+      if (cs != ps) CK(c, cudaStreamSynchronize(cs));
+      dev_free(c, q.codes);
+      q.codes = nullptr;
+      q.codes_rows = 0;
       void* p;
       if ((rc = dev_alloc(c, &p, (uint64_t)c->max_N * c->Vp))) return rc;
-      c->codes = static_cast<uint8_t*>(p);
-      c->codes_rows = c->max_N;
-      CK(c, cudaMemsetAsync(c->codes, 0, (uint64_t)c->max_N * c->Vp, ps));  // padding columns stay U
+      q.codes = static_cast<uint8_t*>(p);
+      q.codes_rows = c->max_N;
+      CK(c, cudaMemsetAsync(q.codes, 0, (uint64_t)c->max_N * c->Vp, cs));  // padding columns stay U
     }
-    // queued on the packing stream: a packing still reading the staging buffer finishes first
-    CK(c, cudaMemcpy2DAsync(c->codes, c->Vp, src, device_src ? pitch : c->V, c->V, n,
-                            device_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ps));
+    if (cs != ps) CK(c, cudaStreamWaitEvent(cs, c->ev_packed[b], 0));
+    CK(c, cudaMemcpy2DAsync(q.codes, c->Vp, src, device_src ? pitch : c->V, c->V, n,
+                            device_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, cs));
+    if (cs != ps) {
+      CK(c, cudaEventRecord(c->ev_staged[b], cs));
+      CK(c, cudaStreamWaitEvent(ps, c->ev_staged[b], 0));
+    }
     if (!device_src) {  // the caller may reuse its host buffer once this call returns
-      CK(c, cudaEventRecord(c->ev_copied, ps));
+      CK(c, cudaEventRecord(c->ev_copied, cs));
       CK(c, cudaEventSynchronize(c->ev_copied));
     }
-    codes = c->codes;
+    codes = q.codes;
     cpitch = c->Vp;
   }
   c->pack_src = codes;

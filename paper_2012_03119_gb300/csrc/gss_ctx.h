@@ -41,7 +41,9 @@ struct gss_ctx {
 
   // assignment sets.  pipeline 1: one plane set, packed and tested on `stream`.  pipeline 2:
   // two plane sets; gss_set_assignments packs into the set the last test did not read, on
-  // pack_stream, so that packing the next set overlaps the test of the last one.
+  // pack_stream, so that packing the next set overlaps the test of the last one, and copies
+  // host values into that set's own staging buffer on copy_stream, so that the next set's
+  // copy need not wait for the last set's packing.
   struct PlaneSet {
     uint32_t* P = nullptr;
     uint32_t* aggF = nullptr;
@@ -49,6 +51,8 @@ struct gss_ctx {
     uint32_t* agg2F = nullptr;  // level-2 rows, held when max_N > GSS_MAX_NARROW_ASSIGNMENTS
     uint32_t* agg2U = nullptr;
     uint32_t N = 0;
+    uint8_t* codes = nullptr;   // staging buffer for values the packing cannot read in place
+    uint64_t codes_rows = 0;
   };
   uint32_t pipeline = 1;
   uint32_t tile_clauses = 0;  // test tile shape (32 or 16); 0: from the mean clause length
@@ -61,11 +65,11 @@ struct gss_ctx {
   cudaEvent_t ev_packed[2] = {nullptr, nullptr};  // pipeline 2: packing of set b done
   cudaEvent_t ev_tested[2] = {nullptr, nullptr};  // pipeline 2: the last test that read set b done
   cudaEvent_t ev_copied = nullptr;  // host codes landed in the staging buffer
+  cudaStream_t copy_stream = nullptr;             // pipeline 2: copies into the staging buffers
+  cudaEvent_t ev_staged[2] = {nullptr, nullptr};  // pipeline 2: the copy into set b's staging buffer done
   uint32_t N = 0, Wp = 4, AWp = 1;  // of the latest assignment set
   bool have_assign = false;
   uint64_t Vp = 0;
-  uint8_t* codes = nullptr;
-  uint64_t codes_rows = 0;
   uint32_t* P = nullptr;      // the latest set's planes (aliases of sets[cur])
   uint32_t* aggF = nullptr;
   uint32_t* aggU = nullptr;

@@ -137,3 +137,30 @@ def test_async_fetch():
             assert e.code == gss.GSS_E_INVAL
         else:
             np.testing.assert_array_equal(gss.expand_reports(ctx.fetch_wait()), want_b)
+
+
+def test_host_sets_alternate_staging_buffers():
+    """Host sets through two plane sets: each set is copied into its own staging buffer on a
+    copy stream, while the last set is packed and tested.  The caller's buffer is free once
+    gss_set_assignments returns (it is overwritten with invalid codes at once), sets of
+    different sizes follow each other, and every test equals the oracle on its own set."""
+    inst = synth.single(scale=0.005)
+    sizes = [1024, 700, 1024, 33, 512, 1024]
+    sets = [c[:n] for c, n in zip(sets_for(inst, len(sizes)), sizes)]
+    want = [oracle.allf_pairs(inst.offsets, inst.lits, c) for c in sets]
+    buf = np.empty((1024, inst.n_vars), np.uint8)
+    with gss.Context(inst.n_vars, max_assignments=1024, report_capacity=1 << 22, pipeline=2) as ctx:
+        ctx.add_clauses(inst.offsets, inst.lits)
+
+        def give(k):
+            n = len(sets[k])
+            buf[:n] = sets[k]
+            ctx.set_assignments(buf[:n])
+            buf[:] = 3  # invalid codes: a copy still reading the buffer would see them
+
+        give(0)
+        for k in range(len(sets)):
+            ctx.test()
+            if k + 1 < len(sets):
+                give(k + 1)
+            np.testing.assert_array_equal(gss.expand_reports(ctx.fetch_reports()), want[k])
