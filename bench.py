@@ -736,14 +736,16 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     # every step copies its codes in and its records out; with two plane sets the codes of step
-    # k + 1 cross the host link while step k's test runs and its records travel back
-    ctx.set_assignments(h_codes.numpy())
+    # k + 1 cross the host link (queued behind step k's copy) while step k is packed and
+    # tested and its records travel back
+    ctx.set_assignments_async(h_codes.numpy())
     for k in range(e2e_steps):
         ctx.test()
         ctx.fetch_reports_async(h_rec)
         if k + 1 < e2e_steps:
-            ctx.set_assignments(h_codes.numpy())
+            ctx.set_assignments_async(h_codes.numpy())
         ctx.fetch_wait()
+    ctx.copy_wait()
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s, dist)
     link_s += host_link_seconds()

@@ -206,6 +206,17 @@ int gss_add_clauses(gss_ctx* ctx, const uint64_t* offsets, uint64_t n_clauses, c
 int gss_set_assignments(gss_ctx* ctx, const uint8_t* values, uint32_t n_assign);
 
 /*
+ * As gss_set_assignments, but returns as soon as the copy is queued: `values` (host memory;
+ * pinned memory lets the copy run while the caller goes on) must stay unchanged until
+ * gss_copy_wait returns.  With two plane sets (gss_config.pipeline = 2) the copy of set k + 1
+ * then queues behind the copy of set k, so that the host link stays busy while the caller
+ * tests set k and reads its records.  gss_copy_wait waits until every host copy queued so far
+ * has read the caller's memory.  Errors as gss_set_assignments.
+ */
+int gss_set_assignments_async(gss_ctx* ctx, const uint8_t* values, uint32_t n_assign);
+int gss_copy_wait(gss_ctx* ctx);
+
+/*
  * As gss_set_assignments, but `d_values` is a DEVICE pointer on the
  * context's device, rows `pitch` bytes apart (pitch >= n_vars), the buffer
  * spanning n_assign * pitch bytes.  Bytes past n_vars in a row are ignored.

@@ -100,6 +100,8 @@ SIGNATURES = {
     "gss_add_clauses": (i32, [P, P, u64, P, P]),
     "gss_set_assignments": (i32, [P, P, u32]),
     "gss_set_assignments_device": (i32, [P, P, u64, u32]),
+    "gss_set_assignments_async": (i32, [P, P, u32]),
+    "gss_copy_wait": (i32, [P]),
     "gss_test": (i32, [P]),
     "gss_fetch_reports": (i32, [P, P, u64, P]),
     "gss_report_count": (i32, [P, P]),
@@ -218,6 +220,21 @@ def gss_set_assignments(ctx, values) -> None:
         _check(ctx, load().gss_set_assignments_device(ctx, ptr, pitch, n))
     else:
         _check(ctx, load().gss_set_assignments(ctx, ptr, n))
+
+
+def gss_set_assignments_async(ctx, values) -> object:
+    """Queue the copy of host ``values`` and return; the returned keepalive (and ``values``)
+    must stay unchanged until gss_copy_wait."""
+    ptr, keep, dev = _host_or_dev(values, np.uint8)
+    if dev:
+        raise ValueError("gss_set_assignments_async takes host values; device values: gss_set_assignments_device")
+    n = keep.shape[0] if keep.ndim == 2 else 0
+    _check(ctx, load().gss_set_assignments_async(ctx, ptr, n))
+    return keep
+
+
+def gss_copy_wait(ctx) -> None:
+    _check(ctx, load().gss_copy_wait(ctx))
 
 
 def gss_set_assignments_device(ctx, d_ptr: int, pitch: int, n_assign: int) -> None:
@@ -345,6 +362,17 @@ class Context:
 
     def set_assignments(self, values) -> None:
         gss_set_assignments(self.ptr, values)
+
+    def set_assignments_async(self, values) -> None:
+        """As set_assignments, but returns once the copy is queued: ``values`` must stay
+        unchanged until copy_wait (pinned memory lets the copy run meanwhile)."""
+        keep = gss_set_assignments_async(self.ptr, values)
+        self.__dict__.setdefault("_copy_keep", []).append(keep)
+
+    def copy_wait(self) -> None:
+        """Wait until every queued host copy has read its values."""
+        gss_copy_wait(self.ptr)
+        self.__dict__.pop("_copy_keep", None)
 
     def test(self) -> None:
         gss_test(self.ptr)

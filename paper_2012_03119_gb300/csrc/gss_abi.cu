@@ -401,7 +401,7 @@ int reserve_db(gss_ctx* c, uint64_t max_clauses, uint64_t max_lits) {
   return GSS_OK;
 }
 
-int stage_assignments(gss_ctx* c, const uint8_t* src, uint64_t pitch, uint32_t n, bool device_src) {
+int stage_assignments(gss_ctx* c, const uint8_t* src, uint64_t pitch, uint32_t n, bool device_src, bool wait_copy) {
   if (!c) return GSS_E_INVAL;
   c->err.clear();
   if (n > c->max_N) return fail(c, GSS_E_INVAL, "n_assign %u > max_assignments %u", n, c->max_N);
@@ -442,15 +442,20 @@ int stage_assignments(gss_ctx* c, const uint8_t* src, uint64_t pitch, uint32_t n
       CK(c, cudaMemsetAsync(q.codes, 0, (uint64_t)c->max_N * c->Vp, cs));  // padding columns stay U
     }
     if (cs != ps) CK(c, cudaStreamWaitEvent(cs, c->ev_packed[b], 0));
-    CK(c, cudaMemcpy2DAsync(q.codes, c->Vp, src, device_src ? pitch : c->V, c->V, n,
-                            device_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, cs));
+    const uint64_t spitch = device_src ? pitch : c->V;
+    const cudaMemcpyKind kind = device_src ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    // rows contiguous on both sides: one linear copy (a pitched copy of the same rows ran 3 % slower)
+    if (spitch == c->V && c->V == c->Vp)
+      CK(c, cudaMemcpyAsync(q.codes, src, (uint64_t)n * c->V, kind, cs));
+    else
+      CK(c, cudaMemcpy2DAsync(q.codes, c->Vp, src, spitch, c->V, n, kind, cs));
     if (cs != ps) {
       CK(c, cudaEventRecord(c->ev_staged[b], cs));
       CK(c, cudaStreamWaitEvent(ps, c->ev_staged[b], 0));
     }
-    if (!device_src) {  // the caller may reuse its host buffer once this call returns
+    if (!device_src) {  // the caller may reuse its host buffer once this call (or gss_copy_wait) returns
       CK(c, cudaEventRecord(c->ev_copied, cs));
-      CK(c, cudaEventSynchronize(c->ev_copied));
+      if (wait_copy) CK(c, cudaEventSynchronize(c->ev_copied));
     }
     codes = q.codes;
     cpitch = c->Vp;
@@ -482,9 +487,10 @@ int pack_staged(gss_ctx* c, cudaStream_t s) {
 
 extern "C" {
 
-static int set_assignments_common(gss_ctx* c, const uint8_t* src, uint64_t pitch, uint32_t n, bool device_src) {
+static int set_assignments_common(gss_ctx* c, const uint8_t* src, uint64_t pitch, uint32_t n, bool device_src,
+                                  bool wait_copy = true) {
   TraceRange tr("gss_set_assignments (pack)");
-  int rc = stage_assignments(c, src, pitch, n, device_src);
+  int rc = stage_assignments(c, src, pitch, n, device_src, wait_copy);
   if (rc) return rc;
   DeviceGuard dg(c->device);
   return pack_staged(c, c->pack_stream);
@@ -492,6 +498,18 @@ static int set_assignments_common(gss_ctx* c, const uint8_t* src, uint64_t pitch
 
 int gss_set_assignments(gss_ctx* c, const uint8_t* values, uint32_t n_assign) {
   return set_assignments_common(c, values, 0, n_assign, false);
+}
+
+int gss_set_assignments_async(gss_ctx* c, const uint8_t* values, uint32_t n_assign) {
+  return set_assignments_common(c, values, 0, n_assign, false, false);
+}
+
+int gss_copy_wait(gss_ctx* c) {
+  if (!c) return GSS_E_INVAL;
+  c->err.clear();
+  DeviceGuard dg(c->device);
+  CK(c, cudaEventSynchronize(c->ev_copied));  // recorded after every host copy, in queue order
+  return GSS_OK;
 }
 
 int gss_set_assignments_device(gss_ctx* c, const uint8_t* d_values, uint64_t pitch, uint32_t n_assign) {

@@ -117,7 +117,9 @@ inline DevStatus* set_status(gss_ctx* c, uint32_t b) { return c->st + set_status
 uint32_t words_stride(uint32_t N);
 uint32_t agg_stride(uint32_t Wp);
 // Copy / register an assignment set without packing it (the batch packs inside its graph).
-int stage_assignments(gss_ctx* c, const uint8_t* src, uint64_t pitch, uint32_t n, bool device_src);
+// wait_copy: return only once host values have been read (else gss_copy_wait does).
+int stage_assignments(gss_ctx* c, const uint8_t* src, uint64_t pitch, uint32_t n, bool device_src,
+                      bool wait_copy = true);
 // Pack the staged assignment set on stream s.
 int pack_staged(gss_ctx* c, cudaStream_t s);
 // Reserve database capacity for max_clauses clauses and max_lits literals, so that later

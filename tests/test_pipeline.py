@@ -164,3 +164,37 @@ def test_host_sets_alternate_staging_buffers():
             if k + 1 < len(sets):
                 give(k + 1)
             np.testing.assert_array_equal(gss.expand_reports(ctx.fetch_reports()), want[k])
+
+
+@pytest.mark.parametrize("pipeline", [1, 2])
+def test_async_host_sets(pipeline):
+    """gss_set_assignments_async returns once the copy is queued (with two plane sets, set k+1's
+    copy queues behind set k's while set k is tested); every test equals the oracle on its set,
+    and after gss_copy_wait the caller's buffers are free: overwriting them changes nothing."""
+    import torch
+    inst = synth.single(scale=0.005)
+    sets = sets_for(inst, 4)
+    want = [oracle.allf_pairs(inst.offsets, inst.lits, c) for c in sets]
+    bufs = []
+    for c in sets:
+        b = torch.empty(c.shape, dtype=torch.uint8).pin_memory().numpy()
+        b[:] = c
+        bufs.append(b)
+    with gss.Context(inst.n_vars, max_assignments=1024, report_capacity=1 << 22, pipeline=pipeline) as ctx:
+        ctx.add_clauses(inst.offsets, inst.lits)
+        ctx.set_assignments_async(bufs[0])
+        for k in range(len(sets)):
+            ctx.test()
+            if k + 1 < len(sets) and pipeline == 2:
+                ctx.set_assignments_async(bufs[k + 1])
+            np.testing.assert_array_equal(gss.expand_reports(ctx.fetch_reports()), want[k])
+            if k + 1 < len(sets) and pipeline == 1:
+                ctx.set_assignments_async(bufs[k + 1])
+        ctx.copy_wait()
+        for b in bufs:
+            b[:] = 3  # invalid codes, written after the wait: no queued copy reads them
+        ctx.test()
+        np.testing.assert_array_equal(gss.expand_reports(ctx.fetch_reports()), want[-1])
+    with pytest.raises(ValueError):
+        with gss.Context(inst.n_vars, max_assignments=1024) as ctx:
+            ctx.set_assignments_async(torch.from_numpy(sets[0]).cuda())
