@@ -650,7 +650,11 @@ int gss_server_submit(gss_server* v, const uint8_t* values, uint32_t n_assign, u
   }
   cudaSetDevice(v->device);
   uint8_t* dst = v->d_slots + (uint64_t)slot * 32u * v->Vp;
-  cudaError_t e = cudaMemcpy2DAsync(dst, v->Vp, values, v->V, v->V, n_assign, cudaMemcpyHostToDevice, v->copy_stream);
+  // rows contiguous on both sides (n_vars a multiple of 16): one linear copy, faster than a pitched one
+  cudaError_t e = v->V == v->Vp
+                      ? cudaMemcpyAsync(dst, values, (uint64_t)n_assign * v->V, cudaMemcpyHostToDevice, v->copy_stream)
+                      : cudaMemcpy2DAsync(dst, v->Vp, values, v->V, v->V, n_assign, cudaMemcpyHostToDevice,
+                                          v->copy_stream);
   if (e == cudaSuccess && n_assign < 32)  // rows past the request are U
     e = cudaMemsetAsync(dst + (uint64_t)n_assign * v->Vp, 0, (uint64_t)(32 - n_assign) * v->Vp, v->copy_stream);
   if (e == cudaSuccess) e = cudaEventRecord(v->slot_ev[slot], v->copy_stream);

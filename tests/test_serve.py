@@ -3,6 +3,7 @@ resident database.  Every request must equal the oracle on the database prefix g
 watermark, and the same request must give the same records alone and in a mix of concurrent
 requests while clauses stream in."""
 import threading
+from concurrent.futures import ThreadPoolExecutor
 import time
 
 import numpy as np
@@ -13,6 +14,19 @@ import synth
 import paper_2012_03119_gb300 as gss
 
 pytestmark = pytest.mark.gpu
+
+
+def submit_together(srv, codes_list):
+    """Submit every request at the same moment, one thread each: requests that arrive while a
+    launch runs join the next one.  Returns the request ids in order."""
+    bar = threading.Barrier(len(codes_list))
+
+    def submit(c):
+        bar.wait()
+        return srv.submit(c, wait_us=10_000_000)
+
+    with ThreadPoolExecutor(len(codes_list)) as ex:
+        return list(ex.map(submit, codes_list))
 
 
 @pytest.fixture(scope="module")
@@ -96,10 +110,10 @@ def test_serve_alone_mixed_and_oracle(work, snaps):
         # continuous batching: requests that arrive while a launch runs join the next one.  The
         # mix above usually shows it; if its timing did not, bursts of back-to-back submissions do
         final = len(work.offsets) - 1
-        for attempt in range(5):
+        for attempt in range(20):
             if st["launches"] < st["words_launched"]:
                 break
-            ids = [(k, srv.submit(snaps[k], wait_us=10_000_000)) for k in range(8)]
+            ids = list(enumerate(submit_together(srv, snaps[:8])))
             for k, rid in ids:
                 rec, info = srv.wait(rid)
                 np.testing.assert_array_equal(gss.expand_reports(rec), prefix_oracle(work, info["watermark"], snaps[k]))
@@ -273,8 +287,8 @@ def test_serve_padding_never_counts_against_capacity(work):
         srv.add_clauses(off, lits)
         alone = [run_alone(srv, c)[0] for c in reqs]
         batched = False
-        for attempt in range(5):  # back to back: later requests join launches together
-            ids = [srv.submit(c, wait_us=10_000_000) for c in reqs]
+        for attempt in range(20):  # submitted at once from several threads: they join launches together
+            ids = submit_together(srv, reqs)
             mixed = [srv.wait(rid) for rid in ids]
             for (rec, info), w in zip(mixed, want):
                 np.testing.assert_array_equal(gss.expand_reports(rec), w)
