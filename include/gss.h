@@ -206,7 +206,8 @@ int gss_add_clauses(gss_ctx* ctx, const uint64_t* offsets, uint64_t n_clauses, c
 int gss_set_assignments(gss_ctx* ctx, const uint8_t* values, uint32_t n_assign);
 
 /*
- * As gss_set_assignments, but returns as soon as the copy is queued: `values` (host memory;
+ * As gss_set_assignments (the same packing, Section 3.4, and aggregates, Section 4.2, of
+ * the same arguments), but returns as soon as the copy is queued: `values` (host memory;
  * pinned memory lets the copy run while the caller goes on) must stay unchanged until
  * gss_copy_wait returns.  With two plane sets (gss_config.pipeline = 2) the copy of set k + 1
  * then queues behind the copy of set k, so that the host link stays busy while the caller
