@@ -425,10 +425,12 @@ int stage_assignments(gss_ctx* c, const uint8_t* src, uint64_t pitch, uint32_t n
   const bool aligned = device_src && pitch % 16 == 0 && (reinterpret_cast<uintptr_t>(src) % 16) == 0;
   if (n && !aligned) {  // host data, or a device layout the packing kernel cannot read as 32-bit words
     // pipeline 1: one staging buffer, the copy queued on the packing stream behind the packing
-    // that still reads it.  pipeline 2: set b's own buffer, copied on copy_stream once the last
-    // packing of set b has read it, and the packing waits for the copy.
+    // that still reads it.  pipeline 2: set b's own buffer; host values are copied on
+    // copy_stream once the last packing of set b has read it, and the packing waits for the
+    // copy.  Device values are copied on pack_stream, where a caller may order the work that
+    // writes them.
     gss_ctx::PlaneSet& q = c->sets[b];
-    cudaStream_t cs = c->pipeline == 2 ? c->copy_stream : ps;
+    cudaStream_t cs = (c->pipeline == 2 && !device_src) ? c->copy_stream : ps;
     if (q.codes_rows < n) {
       CK(c, cudaStreamSynchronize(ps));  // a packing may still read the old buffer
       if (cs != ps) CK(c, cudaStreamSynchronize(cs));

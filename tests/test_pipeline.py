@@ -198,3 +198,28 @@ def test_async_host_sets(pipeline):
     with pytest.raises(ValueError):
         with gss.Context(inst.n_vars, max_assignments=1024) as ctx:
             ctx.set_assignments_async(torch.from_numpy(sets[0]).cuda())
+
+
+def test_device_sets_ordered_on_the_pack_stream():
+    """Device values in a layout the packer cannot read in place (a pitch that is not a multiple
+    of 16) are staged by a copy on pack_stream: values written by work the caller queued on
+    pack_stream, with no host synchronisation, are the ones packed."""
+    import torch
+    inst = synth.single(scale=0.005)  # 5000 vars
+    sets = sets_for(inst, 3)
+    want = [oracle.allf_pairs(inst.offsets, inst.lits, c) for c in sets]
+    N, V = sets[0].shape
+    pitch = V + 3
+    ps = torch.cuda.Stream()
+    pinned = [torch.from_numpy(c).pin_memory() for c in sets]
+    bufs = [torch.zeros((N, pitch), dtype=torch.uint8, device="cuda") for _ in range(2)]
+    torch.cuda.synchronize()
+    with gss.Context(V, max_assignments=1024, report_capacity=1 << 22, pipeline=2, pack_stream=ps) as ctx:
+        ctx.add_clauses(inst.offsets, inst.lits)
+        for k in range(len(sets)):
+            d = bufs[k % 2]
+            with torch.cuda.stream(ps):
+                d[:, :V].copy_(pinned[k], non_blocking=True)  # written on pack_stream
+            gss.gss_set_assignments_device(ctx.ptr, d.data_ptr(), pitch, N)
+            ctx.test()
+            np.testing.assert_array_equal(gss.expand_reports(ctx.fetch_reports()), want[k])
