@@ -527,8 +527,7 @@ int gss_test(gss_ctx* c) {
   const uint32_t b = c->cur;
   DevStatus* st = set_status(c, b);
   if (c->pipeline == 2) CK(c, cudaStreamWaitEvent(c->stream, c->ev_packed[b], 0));  // the set's packing
-  CK(c, cudaMemsetAsync(&st->n_records, 0, 2 * sizeof(unsigned long long), c->stream));  // records, candidates
-  CK(c, cudaMemsetAsync(&st->n_super, 0, sizeof(unsigned long long), c->stream));
+  CK(c, cudaMemsetAsync(&st->n_records, 0, 3 * sizeof(unsigned long long), c->stream));  // records, candidates, super
   if (c->m && c->N) {
     ClauseView db{c->off, c->lits, c->head0, c->head1, 2u * c->V, c->ext};
     PlaneView pv{c->P, c->aggF, c->aggU, c->Wp, c->AWp, c->N, c->V};

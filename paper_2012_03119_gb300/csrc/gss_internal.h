@@ -30,13 +30,14 @@ static_assert(HEAD_K == 16, "kernels read the head as two planes of 8 literals")
 
 // Device-side status words, reset by the host between phases.
 struct DevStatus {
+  // the test's counters, first and together: one memset clears them before a test
   unsigned long long n_records;     // records produced by the last test (may exceed capacity)
   unsigned long long n_candidates;  // (clause, group) pairs that passed the aggregate test (stage A)
+  unsigned long long n_super;       // wide sets: (clause, super-group) pairs that passed the level-2 test
   unsigned int bad_code;         // packing saw a value code outside {0, 1, 2}: bit (w mod 32) for plane word w
   unsigned int bad_lit;          // ingest saw a literal >= 2V
   unsigned int bad_size;         // ingest saw an empty clause or offsets beyond the batch
   unsigned int timeout;          // a bounded device wait gave up
-  unsigned long long n_super;    // wide sets: (clause, super-group) pairs that passed the level-2 test
 };
 
 // Planes of one assignment set.
