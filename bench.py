@@ -731,23 +731,28 @@ def main():
         return out
 
     link_s = host_link_seconds()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    # every step copies its codes in and its records out; with two plane sets the codes of step
-    # k + 1 cross the host link (queued behind step k's copy) while step k is packed and
-    # tested and its records travel back
-    ctx.set_assignments_async(h_codes.numpy())
-    for k in range(e2e_steps):
-        ctx.test()
-        ctx.fetch_reports_async(h_rec)
-        if k + 1 < e2e_steps:
-            ctx.set_assignments_async(h_codes.numpy())
-        ctx.fetch_wait()
-    ctx.copy_wait()
-    e2e_s = time.perf_counter() - t0
-    e2e_s = max_over_ranks(e2e_s, dist)
+    def e2e_loop() -> float:
+        """e2e_steps steps through the API; their wall time (max over ranks)."""
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        # every step copies its codes in and its records out; with two plane sets the codes of
+        # step k + 1 cross the host link (queued behind step k's copy) while step k is packed
+        # and tested and its records travel back
+        ctx.set_assignments_async(h_codes.numpy())
+        for k in range(e2e_steps):
+            ctx.test()
+            ctx.fetch_reports_async(h_rec)
+            if k + 1 < e2e_steps:
+                ctx.set_assignments_async(h_codes.numpy())
+            ctx.fetch_wait()
+        ctx.copy_wait()
+        return max_over_ranks(time.perf_counter() - t0, dist)
+
+    # the host is shared with other jobs: the loop runs three times and the median counts
+    e2e_samples = [e2e_loop() for _ in range(3)]
+    e2e_s = float(np.median(e2e_samples))
     link_s += host_link_seconds()
     link_gbs = N * V / min(link_s) / 1e9
     clk = clocks.stop()
@@ -797,7 +802,9 @@ def main():
                 # the bound the host link sets: one step's codes at the measured copy rate
                 "host_link_GBps": link_gbs, "link_cap_value": m * N * world / (N * V / (link_gbs * 1e9)) / 1e9,
                 "frac_of_link_cap": whole_job_rate(m * N, world, e2e_steps, e2e_s) /
-                (m * N * world / (N * V / (link_gbs * 1e9)) / 1e9)},
+                (m * N * world / (N * V / (link_gbs * 1e9)) / 1e9),
+                "samples": [whole_job_rate(m * N, world, e2e_steps, t) for t in e2e_samples],
+                "steps_per_sample": e2e_steps},
         "roofline": {k: v for k, v in roof[dominant].items()},
         "roofline_all": roof,
         "kernel_only": {"test_tests_per_s_G": m * N / t_test / 1e9, "pack_us": t_pack * 1e6,
